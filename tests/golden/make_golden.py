@@ -1,0 +1,42 @@
+"""Writes the stored expected values under tests/golden/.
+
+Calls only the FP64 oracle (oracle/) and the seeded input generator; never
+the CUDA path.  Re-run after a change to the oracle's arithmetic that the
+paper justifies, and name that passage in the commit message.
+
+    python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+from paper_1706_06750_gb300 import synth  # noqa: E402
+
+
+def main():
+    img = synth.workload_image("256x256")
+    opt = oracle.Options.make(octaves=2, sublevels=4)
+    lv, D, kp, k = oracle.kaze_detect(img, opt)
+    out = {
+        "workload": "256x256, 2 octaves x 4 sublevels, seed 1000",
+        "source": "oracle (FP64), written by tests/golden/make_golden.py",
+        "k": k,
+        "level_mean": [float(x) for x in lv.reshape(lv.shape[0], -1).mean(axis=1)],
+        "level_checksum": [float(np.sum(lv[i] * lv[i])) for i in range(lv.shape[0])],
+        "doh_max": [float(D[i].max()) for i in range(D.shape[0])],
+        "keypoints": [[int(r["level"]), int(r["iy"]), int(r["ix"]),
+                       float(r["x"]), float(r["y"]), float(r["response"])] for r in kp],
+    }
+    with open(os.path.join(HERE, "oracle_256x256.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+
+
+if __name__ == "__main__":
+    main()
