@@ -1,0 +1,219 @@
+/*
+ * kaze.h -- C ABI of the GB300 (sm_103a) KAZE scale-space and detector
+ * library, libkaze.so.
+ *
+ * Method: "GPGPU Acceleration of the KAZE Image Feature Extraction Algorithm"
+ * (arXiv 1706.06750).  The library computes, for one FP32 grayscale image:
+ *   - the nonlinear scale space of Sec. II-A: Gaussian presmoothing, the
+ *     contrast factor k from the gradient histogram (Sec. III-1), the
+ *     Perona-Malik conductance of Eq. 2-3 and the semi-implicit step of
+ *     Eq. 4 solved by additive operator splitting (one tridiagonal solve per
+ *     row and per column), with evolution times from Eq. 6-7;
+ *   - the normalised Hessian-determinant detector response of Eq. 8;
+ *   - 3x3x3 maxima with sub-pixel refinement and the edge test of
+ *     Eq. 9-12 (Sec. II-B, Sec. III-2).
+ *
+ * Conventions shared by every entry point:
+ *   - Images are FP32, row-major, element (x, y) at ptr[y * pitch + x];
+ *     pitch is given in elements (pitch_elems >= w).
+ *   - "d_" pointers are DEVICE pointers (e.g. torch.empty(..., device='cuda')
+ *     .data_ptr()); "h_" pointers are HOST pointers.  The caller owns every
+ *     pointer it passes; the library never frees them.
+ *   - The handle owns its scratch, its level and response buffers.  Pointers
+ *     it hands out (kaze_get_level, kaze_get_response) are borrowed and stay
+ *     valid until the next kaze_build_scale_space / kaze_detect* call on the
+ *     handle or until kaze_destroy.
+ *   - All work is enqueued on the handle's CUDA stream (cudaStream_t passed
+ *     as void*; NULL = legacy default stream).  Only calls that return host
+ *     data synchronise that stream: kaze_get_contrast, kaze_find_extrema,
+ *     kaze_detect, kaze_detect_host and kaze_op_contrast / kaze_op_extrema.
+ *   - Every call returns a kaze_status.  The first CUDA error seen by a
+ *     handle is kept and reported by kaze_last_error; after a KAZE_ERR_CUDA
+ *     the handle should be destroyed.
+ *   - Images smaller than 3x3 or larger than the handle's max_w x max_h give
+ *     KAZE_ERR_INVALID_ARG.
+ */
+#ifndef KAZE_H
+#define KAZE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KAZE_OK = 0,
+    KAZE_ERR_INVALID_ARG = 1,  /* a size, pointer, pitch or option is invalid   */
+    KAZE_ERR_CUDA = 2,         /* a CUDA call or kernel launch failed             */
+    KAZE_ERR_OOM = 3,          /* device allocation failed in kaze_create         */
+    KAZE_ERR_CAPACITY = 4,     /* more keypoints than the output holds            */
+    KAZE_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out              */
+    KAZE_ERR_STATE = 6         /* call out of order (e.g. response before build)  */
+} kaze_status;
+
+/* Conductance functions of Eq. 3. */
+#define KAZE_G1 1  /* g1 = exp(-|grad L_sigma|^2 / k^2)         */
+#define KAZE_G2 2  /* g2 = 1 / (1 + |grad L_sigma|^2 / k^2)     */
+
+/* Normalisation of the Hessian determinant, Eq. 8. */
+#define KAZE_DOH_SIGMA4 0         /* s_i^4 det, s_i = max(1, round(sigma_i)) (default) */
+#define KAZE_DOH_PAPER_LITERAL 1  /* (sigma_i / 2^o_i)^2 det, as Eq. 8 is printed      */
+
+typedef struct kaze_options {
+    int octaves;          /* O of Eq. 6 (>= 1)                                   */
+    int sublevels;        /* S of Eq. 6 (>= 1); N = O*S levels, N <= 64           */
+    float sigma0;         /* base scale of Eq. 6 and presmoothing std (1.6)       */
+    float sigma_d;        /* std of the Gaussian before the gradient (1.0), <= 2  */
+    double k_percentile;  /* percentile of the gradient histogram, (0, 1] (0.7)   */
+    int nbins;            /* histogram bins (300), 1..4096                        */
+    int diffusivity;      /* KAZE_G1 or KAZE_G2 (default)                         */
+    float dthreshold;     /* detector threshold (0.001)                           */
+    float edge_r;         /* edge ratio r of Eq. 12 (10); <= 0 disables the test  */
+    int doh_norm;         /* KAZE_DOH_*                                           */
+    float k_override;     /* > 0: use this contrast factor, skip the histogram    */
+    int max_keypoints;    /* capacity of the device keypoint buffer (65536)       */
+} kaze_options;
+
+/* One detected keypoint (Sec. II-B). */
+typedef struct kaze_keypoint {
+    float x, y;       /* sub-pixel position in full-resolution pixels          */
+    float sigma;      /* sigma_i of the level (Eq. 6)                          */
+    float response;   /* DoH_i at the detected pixel (Eq. 8)                   */
+    float angle;      /* dominant orientation; 0 until described             */
+    int level;        /* i = o*S + s                                           */
+    int octave;       /* o                                                     */
+    int sublevel;     /* s                                                     */
+    int ix, iy;       /* integer pixel at which the 3x3x3 maximum was found    */
+} kaze_keypoint;
+
+typedef struct kaze_handle kaze_handle;
+
+/* Fills *opt with the defaults listed beside each field. */
+void kaze_default_options(kaze_options* opt);
+
+/* Creates a handle for images up to max_w x max_h (both >= 3, <= 16384).
+ * Allocates all device buffers up front (about (2N + 3) * max_w * max_h * 4
+ * bytes).  cuda_stream: the cudaStream_t all work goes to.  On error *out is
+ * NULL.  Errors: INVALID_ARG (bad options or sizes), OOM, CUDA. */
+kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h,
+                        void* cuda_stream, kaze_handle** out);
+
+/* Replaces the handle's stream (work already enqueued stays where it is). */
+kaze_status kaze_set_stream(kaze_handle* h, void* cuda_stream);
+
+/* Builds the nonlinear scale space of Sec. II-A / Sec. III-1 from the device
+ * image d_img (w x h, pitch_elems): L_0 = G_sigma0 * I, k on the device
+ * (no host sync), then for i = 1..N-1 one AOS step of Eq. 4 with
+ * tau = t_i - t_{i-1} (Eq. 7).  Asynchronous. */
+kaze_status kaze_build_scale_space(kaze_handle* h, const float* d_img, int w, int h_,
+                                   int pitch_elems);
+
+/* Borrowed pointer to level L_i (0 <= i < N) of the last build, its pitch in
+ * elements and its evolution time t_i.  Any output pointer may be NULL. */
+kaze_status kaze_get_level(kaze_handle* h, int i, const float** d_level,
+                           int* pitch_elems, float* t_i);
+
+/* Contrast factor k used by the last build (synchronises the stream). */
+kaze_status kaze_get_contrast(kaze_handle* h, float* k);
+
+/* Detector response of Eq. 8 for all N levels of the last build.  Async. */
+kaze_status kaze_detector_response(kaze_handle* h);
+
+/* Borrowed pointer to DoH_i of the last kaze_detector_response. */
+kaze_status kaze_get_response(kaze_handle* h, int i, const float** d_doh, int* pitch_elems);
+
+/* 3x3x3 maxima of the responses (levels 1..N-2, 1-pixel border), sub-pixel
+ * fit and edge test (Sec. II-B, Eq. 9-12).  Copies the keypoints to h_out
+ * sorted by (level, iy, ix) and their total number to *count.  If the total
+ * exceeds capacity (or the handle's max_keypoints), the first entries of the
+ * sorted order that fit are written, *count holds the true total and the
+ * call returns KAZE_ERR_CAPACITY.  h_out may be NULL when capacity is 0.
+ * Synchronises the stream. */
+kaze_status kaze_find_extrema(kaze_handle* h, kaze_keypoint* h_out, int capacity, int* count);
+
+/* kaze_build_scale_space + kaze_detector_response + kaze_find_extrema on a
+ * device image.  The fixed launch sequence is recorded once per image size
+ * and input pointer as a CUDA graph and replayed afterwards; on the legacy
+ * or per-thread default stream, which cannot be captured, the same kernels
+ * are launched one by one.  Synchronises the stream. */
+kaze_status kaze_detect(kaze_handle* h, const float* d_img, int w, int h_, int pitch_elems,
+                        kaze_keypoint* h_out, int capacity, int* count);
+
+/* kaze_detect on a HOST image: copies h_img to the device on the handle's
+ * stream, runs the pipeline, copies the keypoints back.  For overlap the
+ * host buffer should be page-locked (e.g. torch pinned memory). */
+kaze_status kaze_detect_host(kaze_handle* h, const float* h_img, int w, int h_, int pitch_elems,
+                             kaze_keypoint* h_out, int capacity, int* count);
+
+/* ---- single steps, for testing each kernel on given inputs -------------- *
+ * These run one step of the method on caller-owned device buffers on the
+ * handle's stream.  Sizes obey the same limits as kaze_build_scale_space.   */
+
+/* Separable Gaussian (sampled, normalised, radius ceil(3 sigma) <= 16) with
+ * half-sample symmetric borders; in and out may not alias.  Async. */
+kaze_status kaze_op_gaussian(kaze_handle* h, const float* d_in, int in_pitch,
+                             float* d_out, int out_pitch, int w, int h_, float sigma);
+
+/* Contrast factor of Sec. III-1 from base image d_L0 with the handle's
+ * sigma_d, k_percentile and nbins; returns k, hmax and (if h_hist != NULL)
+ * the nbins histogram counts.  Synchronises. */
+kaze_status kaze_op_contrast(kaze_handle* h, const float* d_L0, int pitch, int w, int h_,
+                             float* h_k, float* h_hmax, unsigned int* h_hist);
+
+/* Conductance of Eq. 2-3 (handle's sigma_d and diffusivity) of d_L with
+ * contrast factor k into d_g (same pitch).  Async. */
+kaze_status kaze_op_conductance(kaze_handle* h, const float* d_L, float* d_g, int pitch,
+                                int w, int h_, float k);
+
+/* One AOS step of Eq. 4 with step tau: d_ux receives the row solution,
+ * d_Lnext = (row solution + column solution) / 2.  All buffers share pitch,
+ * which must be a multiple of 4; d_Lnext must not alias d_Lprev or d_g.
+ * Async. */
+kaze_status kaze_op_aos_step(kaze_handle* h, const float* d_Lprev, const float* d_g,
+                             float* d_ux, float* d_Lnext, int pitch, int w, int h_, float tau);
+
+/* Detector response of Eq. 8 of one level: step s = max(1, round(sigma_i)),
+ * normalisation by the handle's doh_norm.  Async. */
+kaze_status kaze_op_doh(kaze_handle* h, const float* d_L, float* d_D, int pitch,
+                        int w, int h_, float sigma_i, int octave);
+
+/* Extrema of a caller-supplied response stack of n levels (level l at
+ * d_D + l * plane_stride, each with the given pitch); level l has scale
+ * sigma[l] (host array).  Output as kaze_find_extrema.  Synchronises. */
+kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch, long long plane_stride,
+                            int w, int h_, int n, const float* h_sigma,
+                            kaze_keypoint* h_out, int capacity, int* count);
+
+/* ---- instrumentation ---------------------------------------------------- */
+
+/* Number of kernel kinds the pipeline launches, and the name of kind k
+ * (presmooth, grad_max, grad_hist, percentile, set_scalar, conductance,
+ * aos_rows, aos_cols, doh, extrema); "" for an unknown kind. */
+int kaze_kernel_kinds(void);
+const char* kaze_kernel_name(int kind);
+
+/* Kernels enqueued by the handle's last pipeline call (kaze_build_scale_space,
+ * kaze_detect, kaze_detect_host or kaze_profile; a replayed graph counts the
+ * kernels it holds); -1 for a NULL handle. */
+int kaze_last_launch_count(const kaze_handle* h);
+
+/* Runs kaze_build_scale_space + kaze_detector_response + the extrema kernel
+ * once, launch by launch (no graph), with a CUDA event pair recorded on the
+ * handle's stream around every kernel.  h_ms[k] receives the summed device
+ * time in ms of kind k, h_launches[k] its number of launches; both arrays
+ * hold kaze_kernel_kinds() entries.  Synchronises the stream. */
+kaze_status kaze_profile(kaze_handle* h, const float* d_img, int w, int h_, int pitch_elems,
+                         double* h_ms, int* h_launches);
+
+/* Static description of a status code. */
+const char* kaze_status_string(kaze_status s);
+
+/* Message of the first error the handle recorded ("" if none). */
+const char* kaze_last_error(const kaze_handle* h);
+
+/* Frees every device buffer and the handle.  NULL is ignored. */
+void kaze_destroy(kaze_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KAZE_H */

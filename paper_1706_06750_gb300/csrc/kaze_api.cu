@@ -1,0 +1,681 @@
+// kaze_api.cu -- host runtime behind the C ABI of include/kaze.h.
+//
+// The handle owns one device arena, carved into: the N evolution levels, the
+// N detector responses, the conductance and row-solution scratch planes, a
+// staging plane for host input, the contrast statistics and the keypoint
+// buffer.  Every plane of a w x h image uses pitch = w rounded up to 32
+// floats (128-byte rows, 16-byte aligned vector access), planes packed
+// back to back.  All work is stream-ordered on the handle's stream; the
+// contrast factor stays on the device so a whole detection can be recorded
+// once as a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kaze_internal.h"
+
+#define KAZE_API extern "C" __attribute__((visibility("default")))
+
+namespace {
+// Kernel kinds, in pipeline order, for launch counting and profiling.
+enum KernelKind {
+    KK_PRESMOOTH = 0, KK_GRAD_MAX, KK_GRAD_HIST, KK_PERCENTILE, KK_SET_SCALAR,
+    KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_COUNT
+};
+const char* const kKindNames[KK_COUNT] = {
+    "presmooth", "grad_max", "grad_hist", "percentile", "set_scalar",
+    "conductance", "aos_rows", "aos_cols", "doh", "extrema"};
+}  // namespace
+
+struct kaze_handle {
+    kaze_options opt;
+    int max_w = 0, max_h = 0, N = 0;
+    cudaStream_t stream = nullptr;
+
+    // device arena and its parts
+    void* arena = nullptr;
+    size_t plane_max = 0;          // floats per plane at max size
+    float* levels = nullptr;       // N planes
+    float* doh = nullptr;          // N planes
+    float* g = nullptr;            // conductance scratch
+    float* ux = nullptr;           // row-solution scratch
+    float* staging = nullptr;      // device copy of a host input image
+    float* d_k = nullptr;          // contrast factor
+    unsigned int* d_hmax = nullptr;
+    unsigned int* d_hist = nullptr;
+    unsigned int* d_count = nullptr;
+    kaze_keypoint* d_kp = nullptr;
+    unsigned int* h_count = nullptr;  // pinned
+
+    // current image geometry
+    int cur_w = 0, cur_h = 0, cur_pitch = 0;
+    long long cur_plane = 0;
+    bool built = false, responded = false;
+
+    // scale table (Eq. 6-7) and filter taps
+    double sigma[kz::kMaxLevels];
+    double t[kz::kMaxLevels];
+    kz::GaussTaps taps0, tapsd;
+    kz::LevelTable tab;
+
+    // recorded detection graph
+    cudaGraphExec_t gexec = nullptr;
+    const float* g_img = nullptr;
+    int g_w = 0, g_h = 0, g_pitch = 0;
+
+    // launch accounting: kernels enqueued by the current pipeline call, and
+    // optional event pairs around each launch (kaze_profile)
+    int launches = 0;
+    int graph_launches = 0;
+    bool profiling = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+
+    std::vector<kaze_keypoint> hkp;
+    std::string err;
+};
+
+namespace {
+
+kaze_status fail(kaze_handle* h, kaze_status s, const std::string& msg)
+{
+    if (h && h->err.empty()) h->err = msg;
+    return s;
+}
+
+kaze_status cuda_fail(kaze_handle* h, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, KAZE_ERR_CUDA, m);
+}
+
+#define KZ_TRY(h, call)                                               \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);      \
+    } while (0)
+
+// Enqueue one kernel of the given kind, counting it and, while profiling,
+// bracketing it with an event pair on the handle's stream.
+#define KZ_LAUNCH(h, kind, call)                                                   \
+    do {                                                                           \
+        cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;                                \
+        if ((h)->profiling) {                                                      \
+            KZ_TRY(h, cudaEventCreate(&ev0_));                                     \
+            KZ_TRY(h, cudaEventCreate(&ev1_));                                     \
+            KZ_TRY(h, cudaEventRecord(ev0_, (h)->stream));                         \
+        }                                                                          \
+        KZ_TRY(h, call);                                                           \
+        (h)->launches += 1;                                                        \
+        if ((h)->profiling) {                                                      \
+            KZ_TRY(h, cudaEventRecord(ev1_, (h)->stream));                         \
+            (h)->prof.push_back({(kind), {ev0_, ev1_}});                           \
+        }                                                                          \
+    } while (0)
+
+#define KZ_CHECK(st) \
+    do {                                   \
+        kaze_status s_ = (st);             \
+        if (s_ != KAZE_OK) return s_;      \
+    } while (0)
+
+int pitch_for(int w) { return (w + 31) / 32 * 32; }
+
+// Sampled normalised Gaussian, radius ceil(3 sigma) (presmoothing and
+// gradient smoothing of Sec. III-1).
+bool make_taps(double sigma, int rmax, kz::GaussTaps* t)
+{
+    int r = (int)std::ceil(3.0 * sigma);
+    if (r < 1) r = 1;
+    if (r > rmax) return false;
+    double w[2 * kz::kMaxGaussR + 1];
+    double sum = 0.0;
+    for (int j = -r; j <= r; ++j) {
+        w[j + r] = std::exp(-(double)j * j / (2.0 * sigma * sigma));
+        sum += w[j + r];
+    }
+    t->r = r;
+    for (int j = 0; j <= 2 * r; ++j) t->w[j] = (float)(w[j] / sum);
+    return true;
+}
+
+int step_of(double sigma)
+{
+    int s = (int)std::floor(sigma + 0.5);
+    return s < 1 ? 1 : s;
+}
+
+kaze_status check_image(kaze_handle* h, int w, int hh)
+{
+    if (w < 3 || hh < 3) return fail(h, KAZE_ERR_INVALID_ARG, "image smaller than 3x3");
+    if (w > h->max_w || hh > h->max_h) return fail(h, KAZE_ERR_INVALID_ARG, "image larger than the handle's maximum");
+    return KAZE_OK;
+}
+
+void set_geometry(kaze_handle* h, int w, int hh)
+{
+    h->cur_w = w;
+    h->cur_h = hh;
+    h->cur_pitch = pitch_for(w);
+    h->cur_plane = (long long)h->cur_pitch * hh;
+}
+
+float* level_ptr(kaze_handle* h, int i) { return h->levels + (size_t)i * h->cur_plane; }
+float* doh_ptr(kaze_handle* h, int i) { return h->doh + (size_t)i * h->cur_plane; }
+
+// Contrast factor k of the base image into h->d_k (device only).
+kaze_status enqueue_contrast(kaze_handle* h, const float* L0, int pitch, int w, int hh)
+{
+    cudaStream_t st = h->stream;
+    if (h->opt.k_override > 0.f) {
+        KZ_LAUNCH(h, KK_SET_SCALAR, kz::launch_set_scalar(h->d_k, h->opt.k_override, st));
+        return KAZE_OK;
+    }
+    KZ_TRY(h, cudaMemsetAsync(h->d_hmax, 0, sizeof(unsigned int), st));
+    KZ_TRY(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned int) * h->opt.nbins, st));
+    KZ_LAUNCH(h, KK_GRAD_MAX, kz::launch_grad_max(L0, pitch, w, hh, h->tapsd, h->d_hmax, st));
+    KZ_LAUNCH(h, KK_GRAD_HIST, kz::launch_grad_hist(L0, pitch, w, hh, h->tapsd, h->d_hmax, h->d_hist, h->opt.nbins, st));
+    KZ_LAUNCH(h, KK_PERCENTILE, kz::launch_percentile(h->d_hist, h->opt.nbins, h->d_hmax, h->opt.k_percentile, h->d_k, st));
+    return KAZE_OK;
+}
+
+// Sec. II-A: presmoothing, k, then N-1 AOS steps (Eq. 4, tau from Eq. 7).
+kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int pitch_elems)
+{
+    cudaStream_t st = h->stream;
+    set_geometry(h, w, hh);
+    const int P = h->cur_pitch;
+    KZ_LAUNCH(h, KK_PRESMOOTH, kz::launch_gaussian(d_img, pitch_elems, level_ptr(h, 0), P, w, hh, h->taps0, st));
+    KZ_CHECK(enqueue_contrast(h, level_ptr(h, 0), P, w, hh));
+    for (int i = 1; i < h->N; ++i) {
+        const float* Lp = level_ptr(h, i - 1);
+        float* Li = level_ptr(h, i);
+        const float tau = (float)(h->t[i] - h->t[i - 1]);
+        KZ_LAUNCH(h, KK_CONDUCTANCE, kz::launch_conductance(Lp, h->g, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
+        KZ_LAUNCH(h, KK_AOS_ROWS, kz::launch_aos_rows(Lp, h->g, h->ux, P, w, hh, tau, st));
+        KZ_LAUNCH(h, KK_AOS_COLS, kz::launch_aos_cols(Lp, h->g, h->ux, Li, P, w, hh, tau, st));
+    }
+    h->built = true;
+    h->responded = false;
+    return KAZE_OK;
+}
+
+kaze_status enqueue_response(kaze_handle* h)
+{
+    KZ_LAUNCH(h, KK_DOH, kz::launch_doh(h->levels, h->doh, h->cur_pitch, h->cur_plane, h->cur_w, h->cur_h, 0, h->N,
+                             h->tab, h->stream));
+    h->responded = true;
+    return KAZE_OK;
+}
+
+kaze_status enqueue_extrema(kaze_handle* h, const float* D, int pitch, long long plane, int w, int hh, int n,
+                            const kz::LevelTable& tab)
+{
+    KZ_TRY(h, cudaMemsetAsync(h->d_count, 0, sizeof(unsigned int), h->stream));
+    KZ_LAUNCH(h, KK_EXTREMA, kz::launch_extrema(D, pitch, plane, w, hh, n, tab, h->opt.dthreshold, h->opt.edge_r, h->d_kp,
+                                 h->opt.max_keypoints, h->d_count, h->stream));
+    KZ_TRY(h, cudaMemcpyAsync(h->h_count, h->d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+    return KAZE_OK;
+}
+
+// After enqueue_extrema: wait, copy the keypoints, sort by (level, iy, ix).
+kaze_status collect_keypoints(kaze_handle* h, kaze_keypoint* out, int capacity, int* count)
+{
+    KZ_TRY(h, cudaStreamSynchronize(h->stream));
+    const unsigned total = *h->h_count;
+    const unsigned have = std::min<unsigned>(total, (unsigned)h->opt.max_keypoints);
+    h->hkp.resize(have);
+    if (have) {
+        KZ_TRY(h, cudaMemcpyAsync(h->hkp.data(), h->d_kp, sizeof(kaze_keypoint) * have, cudaMemcpyDeviceToHost,
+                                  h->stream));
+        KZ_TRY(h, cudaStreamSynchronize(h->stream));
+    }
+    std::sort(h->hkp.begin(), h->hkp.end(), [](const kaze_keypoint& a, const kaze_keypoint& b) {
+        if (a.level != b.level) return a.level < b.level;
+        if (a.iy != b.iy) return a.iy < b.iy;
+        return a.ix < b.ix;
+    });
+    const unsigned cap = capacity > 0 ? (unsigned)capacity : 0u;
+    const unsigned nout = std::min(have, cap);
+    if (nout && out) std::memcpy(out, h->hkp.data(), sizeof(kaze_keypoint) * nout);
+    if (count) *count = (int)total;
+    if (total > cap || total > (unsigned)h->opt.max_keypoints)
+        return fail(h, KAZE_ERR_CAPACITY, "more keypoints than the output capacity");
+    return KAZE_OK;
+}
+
+void drop_graph(kaze_handle* h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->g_img = nullptr;
+}
+
+// Records build + response + extrema once per (input pointer, size) and
+// replays it.
+kaze_status run_detect_graph(kaze_handle* h, const float* d_img, int w, int hh, int pitch)
+{
+    if (h->stream == nullptr || h->stream == cudaStreamLegacy || h->stream == cudaStreamPerThread) {
+        // the default streams cannot be captured: launch the same kernels directly
+        h->launches = 0;
+        KZ_CHECK(enqueue_build(h, d_img, w, hh, pitch));
+        KZ_CHECK(enqueue_response(h));
+        return enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab);
+    }
+    if (!(h->gexec && h->g_img == d_img && h->g_w == w && h->g_h == hh && h->g_pitch == pitch)) {
+        drop_graph(h);
+        cudaGraph_t graph = nullptr;
+        h->launches = 0;
+        KZ_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        kaze_status s = enqueue_build(h, d_img, w, hh, pitch);
+        if (s == KAZE_OK) s = enqueue_response(h);
+        if (s == KAZE_OK) s = enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab);
+        cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+        if (s != KAZE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&h->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            h->gexec = nullptr;
+            return cuda_fail(h, e, "cudaGraphInstantiate");
+        }
+        h->graph_launches = h->launches;
+        h->g_img = d_img;
+        h->g_w = w;
+        h->g_h = hh;
+        h->g_pitch = pitch;
+    }
+    set_geometry(h, w, hh);
+    KZ_TRY(h, cudaGraphLaunch(h->gexec, h->stream));
+    h->launches = h->graph_launches;
+    h->built = true;
+    h->responded = true;
+    return KAZE_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI ----
+
+KAZE_API void kaze_default_options(kaze_options* o)
+{
+    if (!o) return;
+    o->octaves = 4;
+    o->sublevels = 4;
+    o->sigma0 = 1.6f;
+    o->sigma_d = 1.0f;
+    o->k_percentile = 0.7;
+    o->nbins = 300;
+    o->diffusivity = KAZE_G2;
+    o->dthreshold = 0.001f;
+    o->edge_r = 10.0f;
+    o->doh_norm = KAZE_DOH_SIGMA4;
+    o->k_override = 0.0f;
+    o->max_keypoints = 65536;
+}
+
+KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, void* cuda_stream,
+                                 kaze_handle** out)
+{
+    if (!out) return KAZE_ERR_INVALID_ARG;
+    *out = nullptr;
+    kaze_options o;
+    if (opt) o = *opt; else kaze_default_options(&o);
+    const int N = o.octaves * o.sublevels;
+    if (o.octaves < 1 || o.sublevels < 1 || N > kz::kMaxLevels) return KAZE_ERR_INVALID_ARG;
+    if (!(o.sigma0 > 0.f) || !(o.sigma_d > 0.f)) return KAZE_ERR_INVALID_ARG;
+    if (!(o.k_percentile > 0.0 && o.k_percentile <= 1.0)) return KAZE_ERR_INVALID_ARG;
+    if (o.nbins < 1 || o.nbins > kz::kMaxBins) return KAZE_ERR_INVALID_ARG;
+    if (o.diffusivity != KAZE_G1 && o.diffusivity != KAZE_G2) return KAZE_ERR_INVALID_ARG;
+    if (o.doh_norm != KAZE_DOH_SIGMA4 && o.doh_norm != KAZE_DOH_PAPER_LITERAL) return KAZE_ERR_INVALID_ARG;
+    if (o.max_keypoints < 1) return KAZE_ERR_INVALID_ARG;
+    if (max_w < 3 || max_h < 3 || max_w > 16384 || max_h > 16384) return KAZE_ERR_INVALID_ARG;
+    if (kz::aos_rows_smem_bytes(max_w) == 0 || kz::aos_cols_smem_bytes(max_h) == 0) return KAZE_ERR_INVALID_ARG;
+
+    kaze_handle* h = new (std::nothrow) kaze_handle();
+    if (!h) return KAZE_ERR_OOM;
+    h->opt = o;
+    h->N = N;
+    h->max_w = max_w;
+    h->max_h = max_h;
+    h->stream = (cudaStream_t)cuda_stream;
+    if (!make_taps(o.sigma0, kz::kMaxGaussR, &h->taps0) || !make_taps(o.sigma_d, kz::kMaxGradR, &h->tapsd)) {
+        delete h;
+        return KAZE_ERR_INVALID_ARG;
+    }
+    // Eq. 6 (sigma_i = sigma0 2^(o + s/S)) and Eq. 7 (t_i = sigma_i^2 / 2)
+    h->tab.n = N;
+    h->tab.sublevels = o.sublevels;
+    for (int oc = 0; oc < o.octaves; ++oc)
+        for (int s = 0; s < o.sublevels; ++s) {
+            const int i = oc * o.sublevels + s;
+            h->sigma[i] = (double)o.sigma0 * std::pow(2.0, (double)oc + (double)s / o.sublevels);
+            h->t[i] = 0.5 * h->sigma[i] * h->sigma[i];
+            const int st = step_of(h->sigma[i]);
+            h->tab.step[i] = st;
+            h->tab.sigma[i] = (float)h->sigma[i];
+            if (o.doh_norm == KAZE_DOH_PAPER_LITERAL) {
+                const double kn = h->sigma[i] / std::pow(2.0, (double)oc);
+                h->tab.norm[i] = (float)(kn * kn);
+            } else {
+                h->tab.norm[i] = (float)((double)st * st * st * st);
+            }
+        }
+
+    {
+        cudaError_t ce = kz::configure_filter_kernels();
+        if (ce == cudaSuccess) ce = kz::configure_aos_kernels();
+        if (ce == cudaSuccess) ce = kz::configure_detector_kernels();
+        if (ce != cudaSuccess) {
+            delete h;
+            return KAZE_ERR_CUDA;
+        }
+    }
+    const size_t pm = (size_t)pitch_for(max_w) * max_h;
+    h->plane_max = pm;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t bytes = 0;
+    const size_t off_levels = bytes; bytes += al(sizeof(float) * pm * N);
+    const size_t off_doh = bytes;    bytes += al(sizeof(float) * pm * N);
+    const size_t off_g = bytes;      bytes += al(sizeof(float) * pm);
+    const size_t off_ux = bytes;     bytes += al(sizeof(float) * pm);
+    const size_t off_stage = bytes;  bytes += al(sizeof(float) * pm);
+    const size_t off_k = bytes;      bytes += al(sizeof(float));
+    const size_t off_hmax = bytes;   bytes += al(sizeof(unsigned int));
+    const size_t off_hist = bytes;   bytes += al(sizeof(unsigned int) * o.nbins);
+    const size_t off_cnt = bytes;    bytes += al(sizeof(unsigned int));
+    const size_t off_kp = bytes;     bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
+    cudaError_t e = cudaMalloc(&h->arena, bytes);
+    if (e != cudaSuccess) {
+        delete h;
+        return e == cudaErrorMemoryAllocation ? KAZE_ERR_OOM : KAZE_ERR_CUDA;
+    }
+    char* a = (char*)h->arena;
+    h->levels = (float*)(a + off_levels);
+    h->doh = (float*)(a + off_doh);
+    h->g = (float*)(a + off_g);
+    h->ux = (float*)(a + off_ux);
+    h->staging = (float*)(a + off_stage);
+    h->d_k = (float*)(a + off_k);
+    h->d_hmax = (unsigned int*)(a + off_hmax);
+    h->d_hist = (unsigned int*)(a + off_hist);
+    h->d_count = (unsigned int*)(a + off_cnt);
+    h->d_kp = (kaze_keypoint*)(a + off_kp);
+    e = cudaMallocHost(&h->h_count, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        cudaFree(h->arena);
+        delete h;
+        return KAZE_ERR_CUDA;
+    }
+    *h->h_count = 0;
+    *out = h;
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_set_stream(kaze_handle* h, void* cuda_stream)
+{
+    if (!h) return KAZE_ERR_INVALID_ARG;
+    h->stream = (cudaStream_t)cuda_stream;
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_build_scale_space(kaze_handle* h, const float* d_img, int w, int hh, int pitch_elems)
+{
+    if (!h || !d_img) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch_elems < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
+    h->launches = 0;
+    return enqueue_build(h, d_img, w, hh, pitch_elems);
+}
+
+KAZE_API kaze_status kaze_get_level(kaze_handle* h, int i, const float** d_level, int* pitch_elems, float* t_i)
+{
+    if (!h) return KAZE_ERR_INVALID_ARG;
+    if (i < 0 || i >= h->N) return fail(h, KAZE_ERR_INVALID_ARG, "level index out of range");
+    if (!h->built) return fail(h, KAZE_ERR_STATE, "no scale space built yet");
+    if (d_level) *d_level = level_ptr(h, i);
+    if (pitch_elems) *pitch_elems = h->cur_pitch;
+    if (t_i) *t_i = (float)h->t[i];
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_get_contrast(kaze_handle* h, float* k)
+{
+    if (!h || !k) return KAZE_ERR_INVALID_ARG;
+    if (!h->built) return fail(h, KAZE_ERR_STATE, "no scale space built yet");
+    KZ_TRY(h, cudaMemcpyAsync(k, h->d_k, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    KZ_TRY(h, cudaStreamSynchronize(h->stream));
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_detector_response(kaze_handle* h)
+{
+    if (!h) return KAZE_ERR_INVALID_ARG;
+    if (!h->built) return fail(h, KAZE_ERR_STATE, "no scale space built yet");
+    return enqueue_response(h);
+}
+
+KAZE_API kaze_status kaze_get_response(kaze_handle* h, int i, const float** d_doh, int* pitch_elems)
+{
+    if (!h) return KAZE_ERR_INVALID_ARG;
+    if (i < 0 || i >= h->N) return fail(h, KAZE_ERR_INVALID_ARG, "level index out of range");
+    if (!h->responded) return fail(h, KAZE_ERR_STATE, "no detector response computed yet");
+    if (d_doh) *d_doh = doh_ptr(h, i);
+    if (pitch_elems) *pitch_elems = h->cur_pitch;
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_find_extrema(kaze_handle* h, kaze_keypoint* h_out, int capacity, int* count)
+{
+    if (!h || capacity < 0 || (capacity > 0 && !h_out)) return fail(h, KAZE_ERR_INVALID_ARG, "bad output");
+    if (!h->responded) return fail(h, KAZE_ERR_STATE, "no detector response computed yet");
+    KZ_CHECK(enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, h->cur_w, h->cur_h, h->N, h->tab));
+    return collect_keypoints(h, h_out, capacity, count);
+}
+
+KAZE_API kaze_status kaze_detect(kaze_handle* h, const float* d_img, int w, int hh, int pitch_elems,
+                                 kaze_keypoint* h_out, int capacity, int* count)
+{
+    if (!h || !d_img || capacity < 0 || (capacity > 0 && !h_out))
+        return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch_elems < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
+    KZ_CHECK(run_detect_graph(h, d_img, w, hh, pitch_elems));
+    return collect_keypoints(h, h_out, capacity, count);
+}
+
+KAZE_API kaze_status kaze_detect_host(kaze_handle* h, const float* h_img, int w, int hh, int pitch_elems,
+                                      kaze_keypoint* h_out, int capacity, int* count)
+{
+    if (!h || !h_img || capacity < 0 || (capacity > 0 && !h_out))
+        return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch_elems < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
+    const int sp = pitch_for(w);
+    KZ_TRY(h, cudaMemcpy2DAsync(h->staging, sizeof(float) * sp, h_img, sizeof(float) * pitch_elems,
+                                sizeof(float) * w, hh, cudaMemcpyHostToDevice, h->stream));
+    KZ_CHECK(run_detect_graph(h, h->staging, w, hh, sp));
+    return collect_keypoints(h, h_out, capacity, count);
+}
+
+// ---- single steps ----------------------------------------------------------
+
+KAZE_API kaze_status kaze_op_gaussian(kaze_handle* h, const float* d_in, int in_pitch, float* d_out, int out_pitch,
+                                      int w, int hh, float sigma)
+{
+    if (!h || !d_in || !d_out || d_in == d_out) return fail(h, KAZE_ERR_INVALID_ARG, "bad buffers");
+    KZ_CHECK(check_image(h, w, hh));
+    if (in_pitch < w || out_pitch < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
+    kz::GaussTaps t;
+    if (!(sigma > 0.f) || !make_taps(sigma, kz::kMaxGaussR, &t)) return fail(h, KAZE_ERR_INVALID_ARG, "bad sigma");
+    KZ_TRY(h, kz::launch_gaussian(d_in, in_pitch, d_out, out_pitch, w, hh, t, h->stream));
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_op_contrast(kaze_handle* h, const float* d_L0, int pitch, int w, int hh, float* h_k,
+                                      float* h_hmax, unsigned int* h_hist)
+{
+    if (!h || !d_L0) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
+    const float ko = h->opt.k_override;
+    h->opt.k_override = 0.f;  // this op always measures
+    kaze_status s = enqueue_contrast(h, d_L0, pitch, w, hh);
+    h->opt.k_override = ko;
+    KZ_CHECK(s);
+    float k = 0.f;
+    unsigned int hm = 0;
+    KZ_TRY(h, cudaMemcpyAsync(&k, h->d_k, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    KZ_TRY(h, cudaMemcpyAsync(&hm, h->d_hmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+    if (h_hist)
+        KZ_TRY(h, cudaMemcpyAsync(h_hist, h->d_hist, sizeof(unsigned int) * h->opt.nbins, cudaMemcpyDeviceToHost,
+                                  h->stream));
+    KZ_TRY(h, cudaStreamSynchronize(h->stream));
+    if (h_k) *h_k = k;
+    if (h_hmax) {
+        float f;
+        std::memcpy(&f, &hm, sizeof(float));
+        *h_hmax = f;
+    }
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_op_conductance(kaze_handle* h, const float* d_L, float* d_g, int pitch, int w, int hh,
+                                         float k)
+{
+    if (!h || !d_L || !d_g || d_L == d_g) return fail(h, KAZE_ERR_INVALID_ARG, "bad buffers");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch < w || !(k > 0.f)) return fail(h, KAZE_ERR_INVALID_ARG, "bad pitch or k");
+    KZ_TRY(h, kz::launch_set_scalar(h->d_k, k, h->stream));
+    KZ_TRY(h, kz::launch_conductance(d_L, d_g, pitch, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, h->stream));
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_op_aos_step(kaze_handle* h, const float* d_Lprev, const float* d_g, float* d_ux,
+                                      float* d_Lnext, int pitch, int w, int hh, float tau)
+{
+    if (!h || !d_Lprev || !d_g || !d_ux || !d_Lnext) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch < w || pitch % 4) return fail(h, KAZE_ERR_INVALID_ARG, "pitch must be >= w and a multiple of 4");
+    const uintptr_t al = (uintptr_t)d_Lprev | (uintptr_t)d_g | (uintptr_t)d_ux | (uintptr_t)d_Lnext;
+    if (al & 15) return fail(h, KAZE_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    if (d_Lnext == d_Lprev || d_Lnext == d_g || d_ux == d_Lprev || d_ux == d_g)
+        return fail(h, KAZE_ERR_INVALID_ARG, "outputs alias inputs");
+    if (!(tau >= 0.f)) return fail(h, KAZE_ERR_INVALID_ARG, "negative tau");
+    KZ_TRY(h, kz::launch_aos_rows(d_Lprev, d_g, d_ux, pitch, w, hh, tau, h->stream));
+    KZ_TRY(h, kz::launch_aos_cols(d_Lprev, d_g, d_ux, d_Lnext, pitch, w, hh, tau, h->stream));
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_op_doh(kaze_handle* h, const float* d_L, float* d_D, int pitch, int w, int hh,
+                                 float sigma_i, int octave)
+{
+    if (!h || !d_L || !d_D || d_L == d_D) return fail(h, KAZE_ERR_INVALID_ARG, "bad buffers");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch < w || !(sigma_i > 0.f) || octave < 0) return fail(h, KAZE_ERR_INVALID_ARG, "bad pitch/sigma/octave");
+    kz::LevelTable t = h->tab;
+    t.n = 1;
+    t.step[0] = step_of(sigma_i);
+    t.sigma[0] = sigma_i;
+    if (h->opt.doh_norm == KAZE_DOH_PAPER_LITERAL) {
+        const double kn = (double)sigma_i / std::pow(2.0, (double)octave);
+        t.norm[0] = (float)(kn * kn);
+    } else {
+        const double s = t.step[0];
+        t.norm[0] = (float)(s * s * s * s);
+    }
+    KZ_TRY(h, kz::launch_doh(d_L, d_D, pitch, 0, w, hh, 0, 1, t, h->stream));
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch, long long plane_stride, int w,
+                                     int hh, int n, const float* h_sigma, kaze_keypoint* h_out, int capacity,
+                                     int* count)
+{
+    if (!h || !d_D || !h_sigma || capacity < 0 || (capacity > 0 && !h_out))
+        return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch < w || plane_stride < (long long)pitch * hh || n < 1 || n > kz::kMaxLevels)
+        return fail(h, KAZE_ERR_INVALID_ARG, "bad pitch, plane stride or level count");
+    kz::LevelTable t = h->tab;
+    t.n = n;
+    for (int i = 0; i < n; ++i) t.sigma[i] = h_sigma[i];
+    KZ_CHECK(enqueue_extrema(h, d_D, pitch, plane_stride, w, hh, n, t));
+    return collect_keypoints(h, h_out, capacity, count);
+}
+
+KAZE_API int kaze_kernel_kinds(void) { return KK_COUNT; }
+
+KAZE_API const char* kaze_kernel_name(int kind)
+{
+    return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "";
+}
+
+KAZE_API int kaze_last_launch_count(const kaze_handle* h) { return h ? h->launches : -1; }
+
+KAZE_API kaze_status kaze_profile(kaze_handle* h, const float* d_img, int w, int hh, int pitch_elems,
+                                  double* h_ms, int* h_launches)
+{
+    if (!h || !d_img || !h_ms || !h_launches) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch_elems < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
+    for (int k = 0; k < KK_COUNT; ++k) {
+        h_ms[k] = 0.0;
+        h_launches[k] = 0;
+    }
+    h->profiling = true;
+    h->launches = 0;
+    kaze_status s = enqueue_build(h, d_img, w, hh, pitch_elems);
+    if (s == KAZE_OK) s = enqueue_response(h);
+    if (s == KAZE_OK) s = enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab);
+    h->profiling = false;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    for (auto& p : h->prof) {
+        float ms = 0.f;
+        if (s == KAZE_OK && e == cudaSuccess && cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+            h_ms[p.first] += ms;
+            h_launches[p.first] += 1;
+        }
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    h->prof.clear();
+    if (s != KAZE_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return KAZE_OK;
+}
+
+KAZE_API const char* kaze_status_string(kaze_status s)
+{
+    switch (s) {
+        case KAZE_OK: return "ok";
+        case KAZE_ERR_INVALID_ARG: return "invalid argument";
+        case KAZE_ERR_CUDA: return "CUDA error";
+        case KAZE_ERR_OOM: return "out of device memory";
+        case KAZE_ERR_CAPACITY: return "keypoint capacity exceeded";
+        case KAZE_ERR_TIMEOUT: return "device-side wait timed out";
+        case KAZE_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+KAZE_API const char* kaze_last_error(const kaze_handle* h)
+{
+    if (!h) return "null handle";
+    return h->err.c_str();
+}
+
+KAZE_API void kaze_destroy(kaze_handle* h)
+{
+    if (!h) return;
+    drop_graph(h);
+    if (h->arena) cudaFree(h->arena);
+    if (h->h_count) cudaFreeHost(h->h_count);
+    delete h;
+}

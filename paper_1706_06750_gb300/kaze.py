@@ -1,0 +1,407 @@
+"""ctypes binding of libkaze.so (the C ABI of include/kaze.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams; device images are
+2-D float32 CUDA tensors with unit stride along x.  A missing library is an
+error (``KazeError``), never a fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_CUDA = 2
+ERR_OOM = 3
+ERR_CAPACITY = 4
+ERR_TIMEOUT = 5
+ERR_STATE = 6
+
+G1 = 1
+G2 = 2
+DOH_SIGMA4 = 0
+DOH_PAPER_LITERAL = 1
+
+
+class KazeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("octaves", ctypes.c_int),
+        ("sublevels", ctypes.c_int),
+        ("sigma0", ctypes.c_float),
+        ("sigma_d", ctypes.c_float),
+        ("k_percentile", ctypes.c_double),
+        ("nbins", ctypes.c_int),
+        ("diffusivity", ctypes.c_int),
+        ("dthreshold", ctypes.c_float),
+        ("edge_r", ctypes.c_float),
+        ("doh_norm", ctypes.c_int),
+        ("k_override", ctypes.c_float),
+        ("max_keypoints", ctypes.c_int),
+    ]
+
+
+class Keypoint(ctypes.Structure):
+    _fields_ = [
+        ("x", ctypes.c_float), ("y", ctypes.c_float), ("sigma", ctypes.c_float),
+        ("response", ctypes.c_float), ("angle", ctypes.c_float),
+        ("level", ctypes.c_int), ("octave", ctypes.c_int), ("sublevel", ctypes.c_int),
+        ("ix", ctypes.c_int), ("iy", ctypes.c_int),
+    ]
+
+
+KEYPOINT_DTYPE = np.dtype([
+    ("x", np.float32), ("y", np.float32), ("sigma", np.float32), ("response", np.float32),
+    ("angle", np.float32), ("level", np.int32), ("octave", np.int32), ("sublevel", np.int32),
+    ("ix", np.int32), ("iy", np.int32),
+])
+assert KEYPOINT_DTYPE.itemsize == ctypes.sizeof(Keypoint) == 40
+
+_lib = None
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_f = ctypes.c_float
+_SIGNATURES = {
+    "kaze_default_options": (None, [ctypes.POINTER(Options)]),
+    "kaze_create": (_i, [ctypes.POINTER(Options), _i, _i, _vp, ctypes.POINTER(_vp)]),
+    "kaze_set_stream": (_i, [_vp, _vp]),
+    "kaze_build_scale_space": (_i, [_vp, _vp, _i, _i, _i]),
+    "kaze_get_level": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_f)]),
+    "kaze_get_contrast": (_i, [_vp, ctypes.POINTER(_f)]),
+    "kaze_detector_response": (_i, [_vp]),
+    "kaze_get_response": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
+    "kaze_find_extrema": (_i, [_vp, ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
+    "kaze_detect": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
+    "kaze_detect_host": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
+    "kaze_op_gaussian": (_i, [_vp, _vp, _i, _vp, _i, _i, _i, _f]),
+    "kaze_op_contrast": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(_f), ctypes.POINTER(_f),
+                              ctypes.POINTER(ctypes.c_uint)]),
+    "kaze_op_conductance": (_i, [_vp, _vp, _vp, _i, _i, _i, _f]),
+    "kaze_op_aos_step": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _f]),
+    "kaze_op_doh": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _i]),
+    "kaze_op_extrema": (_i, [_vp, _vp, _i, ctypes.c_longlong, _i, _i, _i, ctypes.POINTER(_f),
+                             ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
+    "kaze_kernel_kinds": (_i, []),
+    "kaze_kernel_name": (ctypes.c_char_p, [_i]),
+    "kaze_last_launch_count": (_i, [_vp]),
+    "kaze_profile": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)]),
+    "kaze_status_string": (ctypes.c_char_p, [_i]),
+    "kaze_last_error": (ctypes.c_char_p, [_vp]),
+    "kaze_destroy": (None, [_vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libkaze.so; raises KazeError if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise KazeError(ERR_STATE, f"libkaze.so is not built ({path}); run "
+                                   "paper_1706_06750_gb300.build.build() first")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def default_options(**overrides) -> Options:
+    o = Options()
+    lib().kaze_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class _DeviceView:
+    """Zero-copy __cuda_array_interface__ over a borrowed device plane."""
+
+    def __init__(self, ptr, h, w, pitch):
+        self.__cuda_array_interface__ = {
+            "shape": (h, w), "typestr": "<f4", "data": (int(ptr), False),
+            "strides": (pitch * 4, 4), "version": 3,
+        }
+
+
+def _check_image(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 2
+            and t.stride(1) == 1):
+        raise KazeError(ERR_INVALID_ARG, "expected a 2-D float32 CUDA tensor with unit x-stride")
+    return t.shape[1], t.shape[0], t.stride(0)
+
+
+def _sorted_keypoints(buf, n):
+    return np.frombuffer(buf, dtype=KEYPOINT_DTYPE, count=n).copy()
+
+
+class Kaze:
+    """One library handle: buffers for images up to max_w x max_h."""
+
+    def __init__(self, max_w, max_h, options: Options | None = None, stream=None, **overrides):
+        import torch
+        self._L = lib()
+        opt = options if options is not None else default_options()
+        for k, v in overrides.items():
+            setattr(opt, k, v)
+        self.options = opt
+        if stream is None:
+            # a stream of its own: the legacy default stream cannot be
+            # captured into the detection graph
+            stream = torch.cuda.Stream()
+        self._stream = stream
+        h = _vp()
+        st = self._L.kaze_create(ctypes.byref(opt), int(max_w), int(max_h),
+                                 _vp(stream.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            raise KazeError(st, f"kaze_create failed: {self._L.kaze_status_string(st).decode()}")
+        self._h = h
+        self.max_w, self.max_h = int(max_w), int(max_h)
+        self.n_levels = opt.octaves * opt.sublevels
+        self._w = self._hh = 0
+        self._kp_buf = (Keypoint * opt.max_keypoints)()
+
+    # -- plumbing --
+    def _ck(self, st, what):
+        if st != OK and st != ERR_CAPACITY:
+            msg = self._L.kaze_last_error(self._h).decode()
+            raise KazeError(st, f"{what}: {self._L.kaze_status_string(st).decode()}: {msg}")
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.kaze_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    @property
+    def stream(self):
+        """The torch.cuda.Stream the handle enqueues on."""
+        return self._stream
+
+    def _begin(self):
+        # order the handle's stream after work already queued by the caller
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur != self._stream:
+            self._stream.wait_stream(cur)
+
+    def _end(self):
+        # and the caller's stream after the handle's work
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur != self._stream:
+            cur.wait_stream(self._stream)
+
+    # -- pipeline --
+    def build_scale_space(self, img):
+        w, h, pitch = _check_image(img)
+        self._begin()
+        self._ck(self._L.kaze_build_scale_space(self._h, _vp(img.data_ptr()), w, h, pitch),
+                 "kaze_build_scale_space")
+        self._end()
+        self._w, self._hh = w, h
+
+    def level(self, i, copy=True):
+        import torch
+        p = _vp()
+        pitch = _i()
+        t = _f()
+        self._ck(self._L.kaze_get_level(self._h, int(i), ctypes.byref(p), ctypes.byref(pitch),
+                                        ctypes.byref(t)), "kaze_get_level")
+        v = torch.as_tensor(_DeviceView(p.value, self._hh, self._w, pitch.value), device="cuda")
+        return v.clone() if copy else v
+
+    def levels(self):
+        import torch
+        return torch.stack([self.level(i) for i in range(self.n_levels)])
+
+    def level_time(self, i):
+        t = _f()
+        self._ck(self._L.kaze_get_level(self._h, int(i), None, None, ctypes.byref(t)), "kaze_get_level")
+        return float(t.value)
+
+    def contrast(self):
+        k = _f()
+        self._ck(self._L.kaze_get_contrast(self._h, ctypes.byref(k)), "kaze_get_contrast")
+        return float(k.value)
+
+    def detector_response(self):
+        self._begin()
+        self._ck(self._L.kaze_detector_response(self._h), "kaze_detector_response")
+        self._end()
+
+    def response(self, i, copy=True):
+        import torch
+        p = _vp()
+        pitch = _i()
+        self._ck(self._L.kaze_get_response(self._h, int(i), ctypes.byref(p), ctypes.byref(pitch)),
+                 "kaze_get_response")
+        v = torch.as_tensor(_DeviceView(p.value, self._hh, self._w, pitch.value), device="cuda")
+        return v.clone() if copy else v
+
+    def responses(self):
+        import torch
+        return torch.stack([self.response(i) for i in range(self.n_levels)])
+
+    def find_extrema(self, capacity=None):
+        """Keypoints sorted by (level, iy, ix) as a KEYPOINT_DTYPE array."""
+        cap = self.options.max_keypoints if capacity is None else int(capacity)
+        buf = self._kp_buf if cap <= len(self._kp_buf) else (Keypoint * cap)()
+        n = _i()
+        self._begin()
+        st = self._ck(self._L.kaze_find_extrema(self._h, buf, cap, ctypes.byref(n)), "kaze_find_extrema")
+        self._end()
+        self.last_status = st
+        self.last_count = n.value
+        return _sorted_keypoints(buf, min(n.value, cap))
+
+    def detect(self, img, capacity=None):
+        """Scale space + response + extrema of a device image (graph-replayed)."""
+        w, h, pitch = _check_image(img)
+        cap = self.options.max_keypoints if capacity is None else int(capacity)
+        buf = self._kp_buf if cap <= len(self._kp_buf) else (Keypoint * cap)()
+        n = _i()
+        self._begin()
+        st = self._ck(self._L.kaze_detect(self._h, _vp(img.data_ptr()), w, h, pitch, buf, cap,
+                                          ctypes.byref(n)), "kaze_detect")
+        self._end()
+        self._w, self._hh = w, h
+        self.last_status = st
+        self.last_count = n.value
+        return _sorted_keypoints(buf, min(n.value, cap))
+
+    def detect_host(self, img, capacity=None):
+        """kaze_detect on a host image (numpy array or CPU tensor, float32)."""
+        import torch
+        if isinstance(img, torch.Tensor):
+            if img.is_cuda or img.dtype != torch.float32 or img.dim() != 2 or img.stride(1) != 1:
+                raise KazeError(ERR_INVALID_ARG, "expected a 2-D float32 CPU tensor")
+            ptr, h, w, pitch = img.data_ptr(), img.shape[0], img.shape[1], img.stride(0)
+        else:
+            img = np.ascontiguousarray(img, dtype=np.float32)
+            ptr, (h, w), pitch = img.ctypes.data, img.shape, img.shape[1]
+        cap = self.options.max_keypoints if capacity is None else int(capacity)
+        buf = self._kp_buf if cap <= len(self._kp_buf) else (Keypoint * cap)()
+        n = _i()
+        self._begin()
+        st = self._ck(self._L.kaze_detect_host(self._h, _vp(ptr), w, h, pitch, buf, cap,
+                                               ctypes.byref(n)), "kaze_detect_host")
+        self._end()
+        self._w, self._hh = w, h
+        self.last_status = st
+        self.last_count = n.value
+        return _sorted_keypoints(buf, min(n.value, cap))
+
+    # -- instrumentation --
+    def last_launch_count(self):
+        return int(self._L.kaze_last_launch_count(self._h))
+
+    def profile(self, img):
+        """One eager pipeline pass with per-kernel CUDA events.
+
+        Returns {kernel kind: (summed ms, launches)}."""
+        w, h, pitch = _check_image(img)
+        nk = self._L.kaze_kernel_kinds()
+        ms = (ctypes.c_double * nk)()
+        cnt = (_i * nk)()
+        self._begin()
+        self._ck(self._L.kaze_profile(self._h, _vp(img.data_ptr()), w, h, pitch, ms, cnt), "kaze_profile")
+        self._end()
+        self._w, self._hh = w, h
+        return {self._L.kaze_kernel_name(k).decode(): (float(ms[k]), int(cnt[k])) for k in range(nk)}
+
+    # -- single steps --
+    def op_gaussian(self, src, dst, sigma):
+        w, h, pin = _check_image(src)
+        _, _, pout = _check_image(dst)
+        self._begin()
+        self._ck(self._L.kaze_op_gaussian(self._h, _vp(src.data_ptr()), pin, _vp(dst.data_ptr()), pout,
+                                          w, h, float(sigma)), "kaze_op_gaussian")
+        self._end()
+
+    def op_contrast(self, L0):
+        w, h, pitch = _check_image(L0)
+        k = _f()
+        hm = _f()
+        hist = (ctypes.c_uint * self.options.nbins)()
+        self._begin()
+        self._ck(self._L.kaze_op_contrast(self._h, _vp(L0.data_ptr()), pitch, w, h, ctypes.byref(k),
+                                          ctypes.byref(hm), hist), "kaze_op_contrast")
+        self._end()
+        return float(k.value), float(hm.value), np.array(hist, dtype=np.int64)
+
+    def op_conductance(self, L, g, k):
+        w, h, pitch = _check_image(L)
+        self._begin()
+        self._ck(self._L.kaze_op_conductance(self._h, _vp(L.data_ptr()), _vp(g.data_ptr()), pitch, w, h,
+                                             float(k)), "kaze_op_conductance")
+        self._end()
+
+    def op_aos_step(self, Lprev, g, ux, Lnext, tau):
+        w, h, pitch = _check_image(Lprev)
+        self._begin()
+        self._ck(self._L.kaze_op_aos_step(self._h, _vp(Lprev.data_ptr()), _vp(g.data_ptr()),
+                                          _vp(ux.data_ptr()), _vp(Lnext.data_ptr()), pitch, w, h,
+                                          float(tau)), "kaze_op_aos_step")
+        self._end()
+
+    def op_doh(self, L, D, sigma_i, octave):
+        w, h, pitch = _check_image(L)
+        self._begin()
+        self._ck(self._L.kaze_op_doh(self._h, _vp(L.data_ptr()), _vp(D.data_ptr()), pitch, w, h,
+                                     float(sigma_i), int(octave)), "kaze_op_doh")
+        self._end()
+
+    def op_extrema(self, D, sigma, capacity=None):
+        """D: [n, h, w] float32 CUDA tensor (contiguous rows)."""
+        import torch
+        if not (isinstance(D, torch.Tensor) and D.is_cuda and D.dim() == 3 and D.stride(2) == 1
+                and D.dtype == torch.float32):
+            raise KazeError(ERR_INVALID_ARG, "expected a [n, h, w] float32 CUDA tensor")
+        n, h, w = D.shape
+        sig = (ctypes.c_float * n)(*[float(s) for s in sigma])
+        cap = self.options.max_keypoints if capacity is None else int(capacity)
+        buf = self._kp_buf if cap <= len(self._kp_buf) else (Keypoint * cap)()
+        cnt = _i()
+        self._begin()
+        st = self._ck(self._L.kaze_op_extrema(self._h, _vp(D.data_ptr()), D.stride(1), D.stride(0), w, h, n,
+                                              sig, buf, cap, ctypes.byref(cnt)), "kaze_op_extrema")
+        self._end()
+        self.last_status = st
+        self.last_count = cnt.value
+        return _sorted_keypoints(buf, min(cnt.value, cap))

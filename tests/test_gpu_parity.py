@@ -1,0 +1,349 @@
+"""Parity of the CUDA path with the FP64 oracle (needs a GB300 / sm_103a).
+
+Every call goes through the C ABI of libkaze.so via the ctypes binding.
+Tolerances (FP32 kernels vs FP64 oracle):
+  * scale-space pixels: max |diff| <= 2e-5 (images in [0, 1]);
+  * detector response: max |diff| <= 1e-4 * max |DoH| of the level;
+  * keypoints: same level within 0.5 px, overlap >= 99.5 % after removing
+    keypoints whose admitting decision is within rounding of its boundary;
+  * contrast factor: the same histogram bin or the adjacent one.
+Single-step checks feed both sides the same FP32 input, so they isolate the
+arithmetic of one kernel.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1706_06750_gb300 import synth  # noqa: E402
+
+from kp_match import compare  # noqa: E402
+
+SCALE_TOL = 2e-5
+DOH_REL_TOL = 1e-4
+KP_OVERLAP = 0.995
+
+
+@pytest.fixture(scope="module")
+def kz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_06750_gb300 import build, kaze
+    build.build()
+    oracle.build()
+    return kaze
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def options(kz, **kw):
+    return kz.default_options(**kw)
+
+
+def oracle_options(gpu_opt, k_override=0.0):
+    return oracle.Options.make(
+        octaves=gpu_opt.octaves, sublevels=gpu_opt.sublevels, sigma0=float(gpu_opt.sigma0),
+        sigma_d=float(gpu_opt.sigma_d), k_percentile=gpu_opt.k_percentile, nbins=gpu_opt.nbins,
+        diffusivity=gpu_opt.diffusivity, dthreshold=float(np.float32(gpu_opt.dthreshold)),
+        edge_r=float(gpu_opt.edge_r), doh_norm=gpu_opt.doh_norm, k_override=k_override)
+
+
+def random_smooth(rng, h, w, sigma=1.5):
+    from scipy import ndimage
+    return np.clip(ndimage.gaussian_filter(rng.random((h, w)), sigma) * 1.5 - 0.25, 0, 1)
+
+
+# ------------------------------------------------------------ single steps --
+
+@pytest.mark.parametrize("shape", [(256, 256), (131, 257), (3, 3), (40, 2100), (2100, 40)])
+def test_gaussian_step(kz, shape):
+    rng = np.random.default_rng(1)
+    img = rng.random(shape).astype(np.float32)
+    h, w = shape
+    with kz.Kaze(w, h) as k:
+        src = dev(img)
+        out = torch.empty_like(src)
+        k.op_gaussian(src, out, 1.6)
+        torch.cuda.synchronize()
+    ref = oracle.gaussian(img.astype(np.float64), 1.6)
+    assert np.max(np.abs(host(out) - ref)) < 1e-6
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (131, 257), (1200, 1920)])
+def test_contrast_step(kz, shape):
+    h, w = shape
+    img = synth.image(w, h, 77)
+    L0 = oracle.gaussian(img.astype(np.float64), 1.6).astype(np.float32)
+    with kz.Kaze(w, h) as k:
+        kg, hmax_g, hist_g = k.op_contrast(dev(L0))
+    kr, hmax_r, hist_r, n_r = oracle.contrast_k(L0.astype(np.float64), 1.0, 0.7, 300)
+    assert hmax_g == pytest.approx(hmax_r, rel=1e-5)
+    # A pixel may land in a neighbouring bin only if its FP64 magnitude lies
+    # within FP32 reach of a bin edge; each such pixel moves at most one count
+    # out of one bin and into another.
+    lx, ly = oracle.scharr(oracle.gaussian(L0.astype(np.float64), 1.0))
+    m = np.hypot(lx, ly)[1:-1, 1:-1]
+    u = 300 * m[m > 0] / hmax_r
+    near = int(np.sum(np.abs(u - np.round(u)) < 1e-4)) + int(np.sum(m == 0))
+    assert abs(int(hist_g.sum()) - n_r) <= near
+    assert np.abs(hist_g - hist_r).sum() <= 2 * near
+    width = hmax_r / 300
+    assert abs(kg - kr) <= width * 1.0001 + 1e-7
+
+
+def test_contrast_constant_image_fallback(kz):
+    with kz.Kaze(64, 48) as k:
+        kg, hmax, hist = k.op_contrast(torch.full((48, 64), 0.3, device="cuda"))
+    assert kg == pytest.approx(0.03) and hmax == 0.0 and hist.sum() == 0
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (131, 257), (3, 5)])
+@pytest.mark.parametrize("diff", [2, 1])
+def test_conductance_step(kz, shape, diff):
+    rng = np.random.default_rng(2)
+    h, w = shape
+    L = random_smooth(rng, h, w).astype(np.float32)
+    kval = 0.02
+    with kz.Kaze(w, h, diffusivity=diff) as k:
+        g = torch.empty((h, w), device="cuda")
+        k.op_conductance(dev(L), g, kval)
+        torch.cuda.synchronize()
+    ref = oracle.conductance(L.astype(np.float64), kval, 1.0, diff)
+    # FP32 gradients of values in [0, 1] carry an absolute error of ~5e-7;
+    # |dg/d|grad|| is at most 0.86/k for g1 and 0.65/k for g2, so with
+    # k = 0.02 the conductance may differ by up to ~2e-5.
+    assert np.max(np.abs(host(g) - ref)) < 2e-5
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (131, 257), (3, 3), (4, 61), (61, 4),
+                                   (40, 2100), (2100, 40), (1200, 1920)])
+@pytest.mark.parametrize("tau", [0.53, 67.9])
+def test_aos_step(kz, shape, tau):
+    rng = np.random.default_rng(3)
+    h, w = shape
+    pitch = (w + 31) // 32 * 32
+    L = random_smooth(rng, h, w).astype(np.float32)
+    g = (0.02 + 0.98 * rng.random((h, w))).astype(np.float32)
+    with kz.Kaze(w, h) as k:
+        Lp = torch.zeros((h, pitch), device="cuda")[:, :w]
+        Gp = torch.zeros((h, pitch), device="cuda")[:, :w]
+        Lp.copy_(dev(L))
+        Gp.copy_(dev(g))
+        ux = torch.zeros((h, pitch), device="cuda")[:, :w]
+        ln = torch.zeros((h, pitch), device="cuda")[:, :w]
+        k.op_aos_step(Lp, Gp, ux, ln, tau)
+        torch.cuda.synchronize()
+    rx, ry, rl = oracle.aos_step(L.astype(np.float64), g.astype(np.float64), tau)
+    assert np.max(np.abs(host(ux) - rx)) < 5e-6
+    assert np.max(np.abs(host(ln) - rl)) < 5e-6
+
+
+@pytest.mark.parametrize("s_sigma", [(1.6, 0), (2.69, 0), (9.05, 2), (21.5, 3)])
+def test_doh_step(kz, s_sigma):
+    sigma, octave = s_sigma
+    rng = np.random.default_rng(4)
+    h, w = 131, 257
+    L = random_smooth(rng, h, w, 3.0).astype(np.float32)
+    for norm in (kz.DOH_SIGMA4, kz.DOH_PAPER_LITERAL):
+        with kz.Kaze(w, h, doh_norm=norm) as k:
+            D = torch.empty((h, w), device="cuda")
+            k.op_doh(dev(L), D, sigma, octave)
+            torch.cuda.synchronize()
+        ref = oracle.doh(L.astype(np.float64), sigma, octave, norm)
+        assert np.max(np.abs(host(D) - ref)) <= DOH_REL_TOL * np.max(np.abs(ref))
+
+
+def test_extrema_step_on_identical_responses(kz):
+    # both sides read the same FP32 responses: comparisons are exact, so the
+    # sets agree except for decisions sitting on a sub-pixel/edge boundary
+    img = synth.workload_image("256x256")
+    opt = oracle.Options.make(octaves=2, sublevels=4)
+    lv, _ = oracle.build_scale_space(img, opt)
+    D = oracle.detector_response(lv, opt).astype(np.float32)
+    sig, _ = oracle.scale_table(2, 4, 1.6)
+    with kz.Kaze(256, 256, octaves=2, sublevels=4) as k:
+        kp_g = k.op_extrema(dev(D.reshape(-1, 256)).reshape(8, 256, 256), sig)
+    kp_r = oracle.find_extrema(D.astype(np.float64), oracle.Options.make(
+        octaves=2, sublevels=4, dthreshold=float(np.float32(0.001))))
+    ov, m, ur, ug, md = compare(kp_r, kp_g, D.astype(np.float64))
+    assert not ur and not ug
+    assert len(kp_r) > 20 and ov == 1.0
+    assert md < 1e-4
+
+
+# -------------------------------------------------------------- pipeline --
+
+def run_pipeline(kz, img, octaves, sublevels, k_override=0.0, **kw):
+    h, w = img.shape
+    with kz.Kaze(w, h, octaves=octaves, sublevels=sublevels, k_override=k_override, **kw) as k:
+        x = dev(img)
+        k.build_scale_space(x)
+        kg = k.contrast()
+        levels = host(k.levels())
+        k.detector_response()
+        D = host(k.responses())
+        kp = k.find_extrema()
+    return levels, D, kp, kg
+
+
+def check_pipeline(kz, img, octaves, sublevels, check_k=True, **kw):
+    opt0 = oracle.Options.make(octaves=octaves, sublevels=sublevels)
+    L0 = oracle.gaussian(img.astype(np.float64), 1.6)
+    k_ref, hmax_ref, _, _ = oracle.contrast_k(L0)
+    if check_k:
+        _, _, _, k_gpu = run_pipeline(kz, img, octaves, sublevels)
+        assert abs(k_gpu - k_ref) <= hmax_ref / 300 * 1.0001 + 1e-7
+    # compare the rest with the same k on both sides
+    kf = float(np.float32(k_ref))
+    lv_g, D_g, kp_g, _ = run_pipeline(kz, img, octaves, sublevels, k_override=kf, **kw)
+    opt = oracle.Options.make(octaves=octaves, sublevels=sublevels, k_override=kf,
+                              dthreshold=float(np.float32(0.001)))
+    lv_r, D_r, kp_r, _ = oracle.kaze_detect(img.astype(np.float64), opt)
+    err = np.max(np.abs(lv_g - lv_r), axis=(1, 2))
+    assert np.all(err <= SCALE_TOL), err
+    dmax = np.max(np.abs(D_r), axis=(1, 2))
+    derr = np.max(np.abs(D_g - D_r), axis=(1, 2))
+    assert np.all(derr <= DOH_REL_TOL * dmax + 1e-12), derr / dmax
+    ov, m, ur, ug, md = compare(kp_r, kp_g, D_r)
+    assert ov >= KP_OVERLAP, (ov, len(kp_r), len(kp_g), ur[:3], ug[:3])
+    return lv_g, kp_g, kp_r
+
+
+def test_pipeline_256(kz):
+    img = synth.workload_image("256x256")
+    _, kp_g, kp_r = check_pipeline(kz, img, 2, 4)
+    assert len(kp_r) >= 30
+
+
+def test_pipeline_ragged(kz):
+    img = synth.image(257, 131, 11)
+    check_pipeline(kz, img, 2, 4)
+
+
+def test_pipeline_tiny_and_thin(kz):
+    rng = np.random.default_rng(5)
+    for shape in ((3, 3), (5, 40), (40, 5)):
+        img = rng.random(shape).astype(np.float32)
+        check_pipeline(kz, img, 1, 3)
+
+
+def test_pipeline_g1_and_literal_norm(kz):
+    img = synth.image(200, 150, 12)
+    L0 = oracle.gaussian(img.astype(np.float64), 1.6)
+    k_ref = float(np.float32(oracle.contrast_k(L0)[0]))
+    lv_g, D_g, kp_g, _ = run_pipeline(kz, img, 2, 4, k_override=k_ref, diffusivity=1,
+                                      doh_norm=kz.DOH_PAPER_LITERAL)
+    opt = oracle.Options.make(octaves=2, sublevels=4, k_override=k_ref, diffusivity=1,
+                              doh_norm=oracle.DOH_PAPER_LITERAL, dthreshold=float(np.float32(0.001)))
+    lv_r, D_r, kp_r, _ = oracle.kaze_detect(img.astype(np.float64), opt)
+    assert np.max(np.abs(lv_g - lv_r)) <= SCALE_TOL
+    dmax = np.max(np.abs(D_r), axis=(1, 2))
+    assert np.all(np.max(np.abs(D_g - D_r), axis=(1, 2)) <= DOH_REL_TOL * dmax + 1e-12)
+    ov = compare(kp_r, kp_g, D_r)[0]
+    assert ov >= KP_OVERLAP
+
+
+def test_constant_image(kz):
+    img = np.full((64, 80), 0.42, dtype=np.float32)
+    lv, D, kp, k = run_pipeline(kz, img, 2, 4)
+    assert k == pytest.approx(0.03)
+    assert np.max(np.abs(lv - 0.42)) < 1e-6
+    assert len(kp) == 0
+
+
+def test_mean_preserved_and_max_principle(kz):
+    img = synth.workload_image("256x256")
+    lv, _, _, _ = run_pipeline(kz, img, 2, 4)
+    m0 = lv[0].mean()
+    for i in range(1, lv.shape[0]):
+        assert abs(lv[i].mean() - m0) < 2e-6
+        assert lv[i].min() >= lv[i - 1].min() - 1e-6 and lv[i].max() <= lv[i - 1].max() + 1e-6
+
+
+def test_detect_graph_equals_eager_and_host_path(kz):
+    img = synth.workload_image("256x256")
+    with kz.Kaze(256, 256, octaves=2, sublevels=4) as k:
+        x = dev(img)
+        k.build_scale_space(x)
+        k.detector_response()
+        eager = k.find_extrema()
+        g1 = k.detect(x)
+        g2 = k.detect(x)  # replay
+        hst = k.detect_host(img)
+        pinned = torch.from_numpy(img).pin_memory()
+        hp = k.detect_host(pinned)
+    for other in (g1, g2, hst, hp):
+        assert np.array_equal(eager, other)
+
+
+def test_capacity_overflow_reports_true_count(kz):
+    img = synth.workload_image("256x256")
+    with kz.Kaze(256, 256, octaves=2, sublevels=4) as k:
+        full = k.detect(dev(img))
+        n = len(full)
+        assert n > 5
+        part = k.detect(dev(img), capacity=3)
+        assert k.last_status == kz.ERR_CAPACITY and k.last_count == n
+        assert np.array_equal(part, full[:3])
+    with kz.Kaze(256, 256, octaves=2, sublevels=4, max_keypoints=4) as k:
+        part = k.detect(dev(img))
+        assert k.last_status == kz.ERR_CAPACITY and k.last_count == n and len(part) == 4
+
+
+def test_invalid_arguments(kz):
+    with kz.Kaze(64, 64) as k:
+        with pytest.raises(kz.KazeError) as e:
+            k.build_scale_space(torch.zeros((2, 64), device="cuda"))
+        assert e.value.status == kz.ERR_INVALID_ARG
+        with pytest.raises(kz.KazeError) as e:
+            k.build_scale_space(torch.zeros((65, 64), device="cuda"))
+        assert e.value.status == kz.ERR_INVALID_ARG
+    with kz.Kaze(64, 64) as k:
+        with pytest.raises(kz.KazeError) as e:
+            k.detector_response()
+        assert e.value.status == kz.ERR_STATE
+
+
+# ------------------------------------------------------------- full size --
+
+def test_full_size_1920x1200_against_oracle(kz):
+    img = synth.workload_image("1920x1200")
+    lv_g, kp_g, kp_r = check_pipeline(kz, img, 4, 4)
+    assert len(kp_r) >= 100
+
+
+def test_full_size_4096x3072_sampled_steps(kz):
+    """4096x3072 (12.6 Mpx): GPU run end to end; the oracle recomputes two
+    AOS steps from the GPU's own previous level and the response of one
+    level, and the mean / range invariants hold at every level."""
+    img = synth.workload_image("4096x3072")
+    h, w = img.shape
+    with kz.Kaze(w, h, octaves=4, sublevels=4) as k:
+        x = dev(img)
+        k.build_scale_space(x)
+        kval = k.contrast()
+        k.detector_response()
+        kp = k.find_extrema()
+        sig, t = oracle.scale_table(4, 4, 1.6)
+        means = [float(k.level(i, copy=False).double().mean()) for i in range(16)]
+        for i in (1, 15):
+            Lp = host(k.level(i - 1))
+            Li = host(k.level(i))
+            g = oracle.conductance(Lp, float(kval), 1.0, oracle.G2)
+            _, _, ref = oracle.aos_step(Lp, g, float(np.float32(t[i] - t[i - 1])))
+            assert np.max(np.abs(Li - ref)) <= SCALE_TOL
+        L9 = host(k.level(9))
+        D9 = host(k.response(9))
+        ref = oracle.doh(L9, sig[9], 2)
+        assert np.max(np.abs(D9 - ref)) <= DOH_REL_TOL * np.max(np.abs(ref))
+    assert max(abs(m - means[0]) for m in means) < 1e-5
+    assert len(kp) >= 100
