@@ -90,7 +90,8 @@ typedef struct kaze_handle kaze_handle;
 /* Fills *opt with the defaults listed beside each field. */
 void kaze_default_options(kaze_options* opt);
 
-/* Creates a handle for images up to max_w x max_h (both >= 3, <= 16384).
+/* Creates a handle for images up to max_w x max_h (3 <= max_w <= 16384,
+ * 3 <= max_h <= 6144: a column strip must fit in shared memory).
  * Allocates all device buffers up front (about (2N + 3) * max_w * max_h * 4
  * bytes).  cuda_stream: the cudaStream_t all work goes to.  On error *out is
  * NULL.  Errors: INVALID_ARG (bad options or sizes), OOM, CUDA. */
@@ -166,8 +167,9 @@ kaze_status kaze_op_conductance(kaze_handle* h, const float* d_L, float* d_g, in
 
 /* One AOS step of Eq. 4 with step tau: d_ux receives the row solution,
  * d_Lnext = (row solution + column solution) / 2.  All buffers share pitch,
- * which must be a multiple of 4; d_Lnext must not alias d_Lprev or d_g.
- * Async. */
+ * which must be a multiple of 4, and start on 16-byte boundaries; outputs
+ * must not alias inputs.  Synchronises the stream (it reports a timed-out
+ * device wait as KAZE_ERR_TIMEOUT). */
 kaze_status kaze_op_aos_step(kaze_handle* h, const float* d_Lprev, const float* d_g,
                              float* d_ux, float* d_Lnext, int pitch, int w, int h_, float tau);
 
@@ -207,7 +209,8 @@ kaze_status kaze_profile(kaze_handle* h, const float* d_img, int w, int h_, int 
 /* Static description of a status code. */
 const char* kaze_status_string(kaze_status s);
 
-/* Message of the first error the handle recorded ("" if none). */
+/* Message of the first error the handle recorded ("" if none).  With
+ * h == NULL: why the calling thread's last failed kaze_create failed. */
 const char* kaze_last_error(const kaze_handle* h);
 
 /* Frees every device buffer and the handle.  NULL is ignored. */

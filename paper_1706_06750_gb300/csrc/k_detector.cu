@@ -133,7 +133,7 @@ k_extrema(const float* __restrict__ D, int pitch, long long plane_stride, int w,
 
 cudaError_t configure_detector_kernels()
 {
-    return cudaFuncSetAttribute(k_doh, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    return allow_max_dynamic_smem(k_doh);
 }
 
 cudaError_t launch_doh(const float* L, float* D, int pitch, long long plane_stride, int w, int h,

@@ -20,94 +20,114 @@ constexpr int TY = 32;  // output tile height
 constexpr int BX = 32;  // threads per CTA, x
 constexpr int BY = 8;   // threads per CTA, y
 
-// Separable Gaussian: rows first, then columns (same order as the method's
-// definition of the presmoothing).
+// Separable Gaussian of radius R: rows first, then columns (the order of the
+// method's definition of the presmoothing).  Loops have compile-time trip
+// counts so each thread issues all of its staging loads before storing.
+template <int R>
 __global__ void __launch_bounds__(BX* BY)
 k_gaussian(const float* __restrict__ in, int in_pitch, float* __restrict__ out, int out_pitch,
            int w, int h, const __grid_constant__ GaussTaps taps)
 {
-    extern __shared__ float sm[];
-    const int r = taps.r;
-    const int SW = TX + 2 * r;
-    const int SH = TY + 2 * r;
-    float* A = sm;            // SH x SW input tile
-    float* B = sm + SH * SW;  // SH x TX row-filtered tile
+    constexpr int SW = TX + 2 * R, SH = TY + 2 * R;
+    __shared__ float A[SH][SW + 1];  // input tile
+    __shared__ float B[SH][TX + 1];  // row-filtered tile
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.y * BX + threadIdx.x;
-    constexpr int NT = BX * BY;
+    const int tx = threadIdx.x, ty = threadIdx.y;
 
-    for (int i = tid; i < SH * SW; i += NT) {
-        int sy = i / SW, sx = i - sy * SW;
-        int gy = reflect_index(y0 - r + sy, h), gx = reflect_index(x0 - r + sx, w);
-        A[i] = __ldg(in + (size_t)gy * in_pitch + gx);
+    int gx[(SW + BX - 1) / BX];
+#pragma unroll
+    for (int k = 0; k < (SW + BX - 1) / BX; ++k) gx[k] = reflect_index(x0 - R + tx + k * BX, w);
+#pragma unroll
+    for (int sy = ty; sy < SH; sy += BY) {
+        const float* row = in + (size_t)reflect_index(y0 - R + sy, h) * in_pitch;
+#pragma unroll
+        for (int k = 0; k < (SW + BX - 1) / BX; ++k)
+            if (tx + k * BX < SW) A[sy][tx + k * BX] = __ldg(row + gx[k]);
     }
     __syncthreads();
-    for (int i = tid; i < SH * TX; i += NT) {
-        int sy = i / TX, sx = i - sy * TX;
-        const float* a = A + sy * SW + sx;
+#pragma unroll
+    for (int sy = ty; sy < SH; sy += BY) {
         float acc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], a[j], acc);
-        B[i] = acc;
+#pragma unroll
+        for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], A[sy][tx + j], acc);
+        B[sy][tx] = acc;
     }
     __syncthreads();
-    for (int ty = threadIdx.y; ty < TY; ty += BY) {
-        int gx = x0 + threadIdx.x, gy = y0 + ty;
-        if (gx >= w || gy >= h) continue;
-        const float* b = B + ty * TX + threadIdx.x;
+    const int ox = x0 + tx;
+#pragma unroll
+    for (int oy = ty; oy < TY; oy += BY) {
         float acc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], b[j * TX], acc);
-        out[(size_t)gy * out_pitch + gx] = acc;
+#pragma unroll
+        for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], B[oy + j][tx], acc);
+        if (ox < w && y0 + oy < h) out[(size_t)(y0 + oy) * out_pitch + ox] = acc;
     }
 }
 
 enum GradMode { MODE_COND = 0, MODE_MAX = 1, MODE_HIST = 2 };
 
-// Smoothed Scharr gradient of a 32x32 tile.  Stages L with a halo of r+1,
-// smooths with G(sigma_d) on a (32+2)^2 region, then applies the 3x3 Scharr
-// pair ([-1 0 1]/2 x [3 10 3]/16 and its transpose).  MODE_COND writes the
-// conductance g of Eq. 3; MODE_MAX folds |grad| of interior pixels into a
-// global maximum; MODE_HIST bins the non-zero interior magnitudes.
-template <int MODE>
+// Smoothed Scharr gradient of a 32x32 tile.  Stages L with a halo of R+1,
+// smooths with G(sigma_d) (radius R) on the (32+2)^2 region around the tile,
+// then applies the 3x3 Scharr pair ([-1 0 1]/2 x [3 10 3]/16 and its
+// transpose).  MODE_COND writes the conductance g of Eq. 3; MODE_MAX folds
+// |grad| of interior pixels into a global maximum; MODE_HIST bins the
+// non-zero interior magnitudes.
+template <int MODE, int R>
 __global__ void __launch_bounds__(BX* BY)
 k_gradient(const float* __restrict__ L, float* __restrict__ g, int pitch, int w, int h,
            const __grid_constant__ GaussTaps taps, const float* __restrict__ d_k, int diffusivity,
            unsigned int* __restrict__ d_hmax_bits, unsigned int* __restrict__ d_hist, int nbins)
 {
-    extern __shared__ float sm[];
-    const int r = taps.r;
-    constexpr int CW = TX + 2, CH = TY + 2;  // smoothed region (halo 1 for Scharr)
-    const int SW = CW + 2 * r, SH = CH + 2 * r;
-    float* A = sm;                 // SH x SW   raw L
-    float* B = A + SH * SW;        // SH x CW   row-smoothed
-    float* C = B + SH * CW;        // CH x CW   smoothed
+    constexpr int CW = TX + 2, CH = TY + 2;      // smoothed region (halo 1 for Scharr)
+    constexpr int SW = CW + 2 * R, SH = CH + 2 * R;
+    constexpr int KX = (SW + BX - 1) / BX;
+    __shared__ float A[SH][SW + 1];  // raw L
+    __shared__ float B[SH][CW + 1];  // row-smoothed
+    __shared__ float C[CH][CW + 1];  // smoothed
+    extern __shared__ unsigned int hist_s[];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.y * BX + threadIdx.x;
-    constexpr int NT = BX * BY;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * BX + tx;
 
-    unsigned int* hist_s = reinterpret_cast<unsigned int*>(C + CH * CW);
     if (MODE == MODE_HIST) {
-        for (int i = tid; i < nbins; i += NT) hist_s[i] = 0u;
+        for (int i = tid; i < nbins; i += BX * BY) hist_s[i] = 0u;
     }
-    for (int i = tid; i < SH * SW; i += NT) {
-        int sy = i / SW, sx = i - sy * SW;
-        int gy = reflect_index(y0 - 1 - r + sy, h), gx = reflect_index(x0 - 1 - r + sx, w);
-        A[i] = __ldg(L + (size_t)gy * pitch + gx);
-    }
-    __syncthreads();
-    for (int i = tid; i < SH * CW; i += NT) {
-        int sy = i / CW, sx = i - sy * CW;
-        const float* a = A + sy * SW + sx;
-        float acc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], a[j], acc);
-        B[i] = acc;
+    int gx[KX];
+#pragma unroll
+    for (int k = 0; k < KX; ++k) gx[k] = reflect_index(x0 - 1 - R + tx + k * BX, w);
+#pragma unroll
+    for (int sy = ty; sy < SH; sy += BY) {
+        const float* row = L + (size_t)reflect_index(y0 - 1 - R + sy, h) * pitch;
+#pragma unroll
+        for (int k = 0; k < KX; ++k)
+            if (tx + k * BX < SW) A[sy][tx + k * BX] = __ldg(row + gx[k]);
     }
     __syncthreads();
-    for (int i = tid; i < CH * CW; i += NT) {
-        int sy = i / CW, sx = i - sy * CW;
-        const float* b = B + sy * CW + sx;
-        float acc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], b[j * CW], acc);
-        C[i] = acc;
+#pragma unroll
+    for (int sy = ty; sy < SH; sy += BY) {
+#pragma unroll
+        for (int k = 0; k < (CW + BX - 1) / BX; ++k) {
+            const int sx = tx + k * BX;
+            if (sx < CW) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], A[sy][sx + j], acc);
+                B[sy][sx] = acc;
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int sy = ty; sy < CH; sy += BY) {
+#pragma unroll
+        for (int k = 0; k < (CW + BX - 1) / BX; ++k) {
+            const int sx = tx + k * BX;
+            if (sx < CW) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], B[sy + j][sx], acc);
+                C[sy][sx] = acc;
+            }
+        }
     }
     __syncthreads();
 
@@ -116,26 +136,27 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, int pitch, int w,
     if (MODE == MODE_HIST) hmax = __uint_as_float(*d_hmax_bits);
     float local_max = 0.f;
     const float c0 = 3.f / 16.f, c1 = 10.f / 16.f;
+    const int gxo = x0 + tx;
 
-    for (int ty = threadIdx.y; ty < TY; ty += BY) {
-        const int tx = threadIdx.x;
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (gx >= w || gy >= h) continue;
-        // C(cx, cy) holds the smoothed value at (x0 - 1 + cx, y0 - 1 + cy).
-        const float* c = C + (ty + 1) * CW + (tx + 1);
-        float lx = c0 * 0.5f * (c[-CW + 1] - c[-CW - 1]);
-        lx += c1 * 0.5f * (c[1] - c[-1]);
-        lx += c0 * 0.5f * (c[CW + 1] - c[CW - 1]);
-        float ly = c0 * 0.5f * (c[CW - 1] - c[-CW - 1]);
-        ly += c1 * 0.5f * (c[CW] - c[-CW]);
-        ly += c0 * 0.5f * (c[CW + 1] - c[-CW + 1]);
+#pragma unroll
+    for (int oy = ty; oy < TY; oy += BY) {
+        const int gy = y0 + oy;
+        // C[cy][cx] holds the smoothed value at (x0 - 1 + cx, y0 - 1 + cy)
+        const int cy = oy + 1, cx = tx + 1;
+        float lx = c0 * 0.5f * (C[cy - 1][cx + 1] - C[cy - 1][cx - 1]);
+        lx += c1 * 0.5f * (C[cy][cx + 1] - C[cy][cx - 1]);
+        lx += c0 * 0.5f * (C[cy + 1][cx + 1] - C[cy + 1][cx - 1]);
+        float ly = c0 * 0.5f * (C[cy + 1][cx - 1] - C[cy - 1][cx - 1]);
+        ly += c1 * 0.5f * (C[cy + 1][cx] - C[cy - 1][cx]);
+        ly += c0 * 0.5f * (C[cy + 1][cx + 1] - C[cy - 1][cx + 1]);
+        if (gxo >= w || gy >= h) continue;
         if (MODE == MODE_COND) {
-            float q = (lx * lx + ly * ly) / (kk * kk);
-            g[(size_t)gy * pitch + gx] = diffusivity == KAZE_G1 ? expf(-q) : 1.f / (1.f + q);
+            const float q = (lx * lx + ly * ly) / (kk * kk);
+            g[(size_t)gy * pitch + gxo] = diffusivity == KAZE_G1 ? expf(-q) : 1.f / (1.f + q);
         } else {
-            bool interior = gx >= 1 && gx <= w - 2 && gy >= 1 && gy <= h - 2;
+            const bool interior = gxo >= 1 && gxo <= w - 2 && gy >= 1 && gy <= h - 2;
             if (!interior) continue;
-            float m = sqrtf(lx * lx + ly * ly);
+            const float m = sqrtf(lx * lx + ly * ly);
             if (MODE == MODE_MAX) {
                 local_max = fmaxf(local_max, m);
             } else if (m > 0.f) {
@@ -148,12 +169,12 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, int pitch, int w,
     if (MODE == MODE_MAX) {
         for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
         // non-negative floats order like their bit patterns
-        if (threadIdx.x == 0 && local_max > 0.f) atomicMax(d_hmax_bits, __float_as_uint(local_max));
+        if (tx == 0 && local_max > 0.f) atomicMax(d_hmax_bits, __float_as_uint(local_max));
     }
     if (MODE == MODE_HIST) {
         __syncthreads();
-        for (int i = tid; i < nbins; i += NT) {
-            unsigned int v = hist_s[i];
+        for (int i = tid; i < nbins; i += BX * BY) {
+            const unsigned int v = hist_s[i];
             if (v) atomicAdd(&d_hist[i], v);
         }
     }
@@ -203,23 +224,38 @@ __global__ void k_percentile(const unsigned int* __restrict__ hist, int nbins,
 
 __global__ void k_set_scalar(float* d, float v) { *d = v; }
 
-size_t gradient_smem(int r, int nbins, int mode)
+template <int MODE, int R>
+cudaError_t launch_gradient_r(const float* L, float* g, int pitch, int w, int h, const GaussTaps& taps,
+                              const float* d_k, int diffusivity, unsigned int* hmax_bits, unsigned int* hist,
+                              int nbins, cudaStream_t st)
 {
-    const int CW = TX + 2, CH = TY + 2;
-    const int SW = CW + 2 * r, SH = CH + 2 * r;
-    size_t f = (size_t)SH * SW + (size_t)SH * CW + (size_t)CH * CW;
-    return f * sizeof(float) + (mode == MODE_HIST ? (size_t)nbins * sizeof(unsigned int) : 0);
+    dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY);
+    const size_t smem = MODE == MODE_HIST ? (size_t)nbins * sizeof(unsigned int) : 0;
+    k_gradient<MODE, R><<<grid, dim3(BX, BY), smem, st>>>(L, g, pitch, w, h, taps, d_k, diffusivity, hmax_bits,
+                                                         hist, nbins);
+    return cudaGetLastError();
 }
 
 template <int MODE>
 cudaError_t launch_gradient(const float* L, float* g, int pitch, int w, int h, const GaussTaps& taps,
-                            const float* d_k, int diffusivity, unsigned int* hmax_bits,
-                            unsigned int* hist, int nbins, cudaStream_t st)
+                            const float* d_k, int diffusivity, unsigned int* hmax_bits, unsigned int* hist,
+                            int nbins, cudaStream_t st)
+{
+    switch (taps.r) {
+#define KZ_GRAD_CASE(RR) \
+    case RR: return launch_gradient_r<MODE, RR>(L, g, pitch, w, h, taps, d_k, diffusivity, hmax_bits, hist, nbins, st);
+        KZ_GRAD_CASE(1) KZ_GRAD_CASE(2) KZ_GRAD_CASE(3) KZ_GRAD_CASE(4) KZ_GRAD_CASE(5) KZ_GRAD_CASE(6)
+#undef KZ_GRAD_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R>
+cudaError_t launch_gaussian_r(const float* in, int in_pitch, float* out, int out_pitch, int w, int h,
+                              const GaussTaps& taps, cudaStream_t st)
 {
     dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY);
-    size_t smem = gradient_smem(taps.r, nbins, MODE);
-    k_gradient<MODE><<<grid, dim3(BX, BY), smem, st>>>(L, g, pitch, w, h, taps, d_k, diffusivity,
-                                                       hmax_bits, hist, nbins);
+    k_gaussian<R><<<grid, dim3(BX, BY), 0, st>>>(in, in_pitch, out, out_pitch, w, h, taps);
     return cudaGetLastError();
 }
 
@@ -227,22 +263,22 @@ cudaError_t launch_gradient(const float* L, float* g, int pitch, int w, int h, c
 
 cudaError_t configure_filter_kernels()
 {
-    const int cap = kMaxDynSmem;
-    cudaError_t e = cudaFuncSetAttribute(k_gaussian, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gradient<MODE_COND>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gradient<MODE_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gradient<MODE_HIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    return e;
+    // static shared memory only (the histogram's dynamic part is <= 16 KB)
+    return cudaSuccess;
 }
 
 cudaError_t launch_gaussian(const float* in, int in_pitch, float* out, int out_pitch, int w, int h,
                             const GaussTaps& taps, cudaStream_t st)
 {
-    const int r = taps.r;
-    size_t smem = ((size_t)(TY + 2 * r) * (TX + 2 * r) + (size_t)(TY + 2 * r) * TX) * sizeof(float);
-    dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY);
-    k_gaussian<<<grid, dim3(BX, BY), smem, st>>>(in, in_pitch, out, out_pitch, w, h, taps);
-    return cudaGetLastError();
+    switch (taps.r) {
+#define KZ_GAUSS_CASE(RR) \
+    case RR: return launch_gaussian_r<RR>(in, in_pitch, out, out_pitch, w, h, taps, st);
+        KZ_GAUSS_CASE(1) KZ_GAUSS_CASE(2) KZ_GAUSS_CASE(3) KZ_GAUSS_CASE(4) KZ_GAUSS_CASE(5) KZ_GAUSS_CASE(6)
+        KZ_GAUSS_CASE(7) KZ_GAUSS_CASE(8) KZ_GAUSS_CASE(9) KZ_GAUSS_CASE(10) KZ_GAUSS_CASE(11) KZ_GAUSS_CASE(12)
+        KZ_GAUSS_CASE(13) KZ_GAUSS_CASE(14) KZ_GAUSS_CASE(15) KZ_GAUSS_CASE(16)
+#undef KZ_GAUSS_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_conductance(const float* L, float* g, int pitch, int w, int h, const GaussTaps& taps,

@@ -48,8 +48,10 @@ struct kaze_handle {
     unsigned int* d_hmax = nullptr;
     unsigned int* d_hist = nullptr;
     unsigned int* d_count = nullptr;
+    int* d_status = nullptr;         // bit 0: a bounded device wait ran out
     kaze_keypoint* d_kp = nullptr;
     unsigned int* h_count = nullptr;  // pinned
+    int* h_status = nullptr;          // pinned
 
     // current image geometry
     int cur_w = 0, cur_h = 0, cur_pitch = 0;
@@ -80,9 +82,18 @@ struct kaze_handle {
 
 namespace {
 
+// Message of the last kaze_create that failed on this thread.
+thread_local std::string g_create_err;
+
 kaze_status fail(kaze_handle* h, kaze_status s, const std::string& msg)
 {
     if (h && h->err.empty()) h->err = msg;
+    return s;
+}
+
+kaze_status create_fail(kaze_status s, const std::string& msg)
+{
+    g_create_err = msg;
     return s;
 }
 
@@ -188,6 +199,7 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
     cudaStream_t st = h->stream;
     set_geometry(h, w, hh);
     const int P = h->cur_pitch;
+    KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
     KZ_LAUNCH(h, KK_PRESMOOTH, kz::launch_gaussian(d_img, pitch_elems, level_ptr(h, 0), P, w, hh, h->taps0, st));
     KZ_CHECK(enqueue_contrast(h, level_ptr(h, 0), P, w, hh));
     for (int i = 1; i < h->N; ++i) {
@@ -195,8 +207,8 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
         float* Li = level_ptr(h, i);
         const float tau = (float)(h->t[i] - h->t[i - 1]);
         KZ_LAUNCH(h, KK_CONDUCTANCE, kz::launch_conductance(Lp, h->g, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
-        KZ_LAUNCH(h, KK_AOS_ROWS, kz::launch_aos_rows(Lp, h->g, h->ux, P, w, hh, tau, st));
-        KZ_LAUNCH(h, KK_AOS_COLS, kz::launch_aos_cols(Lp, h->g, h->ux, Li, P, w, hh, tau, st));
+        KZ_LAUNCH(h, KK_AOS_ROWS, kz::launch_aos_rows(Lp, h->g, h->ux, P, w, hh, tau, h->d_status, st));
+        KZ_LAUNCH(h, KK_AOS_COLS, kz::launch_aos_cols(Lp, h->g, h->ux, Li, P, w, hh, tau, h->d_status, st));
     }
     h->built = true;
     h->responded = false;
@@ -218,6 +230,7 @@ kaze_status enqueue_extrema(kaze_handle* h, const float* D, int pitch, long long
     KZ_LAUNCH(h, KK_EXTREMA, kz::launch_extrema(D, pitch, plane, w, hh, n, tab, h->opt.dthreshold, h->opt.edge_r, h->d_kp,
                                  h->opt.max_keypoints, h->d_count, h->stream));
     KZ_TRY(h, cudaMemcpyAsync(h->h_count, h->d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+    KZ_TRY(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     return KAZE_OK;
 }
 
@@ -225,6 +238,7 @@ kaze_status enqueue_extrema(kaze_handle* h, const float* D, int pitch, long long
 kaze_status collect_keypoints(kaze_handle* h, kaze_keypoint* out, int capacity, int* count)
 {
     KZ_TRY(h, cudaStreamSynchronize(h->stream));
+    if (*h->h_status) return fail(h, KAZE_ERR_TIMEOUT, "a bounded device-side wait ran out");
     const unsigned total = *h->h_count;
     const unsigned have = std::min<unsigned>(total, (unsigned)h->opt.max_keypoints);
     h->hkp.resize(have);
@@ -323,23 +337,28 @@ KAZE_API void kaze_default_options(kaze_options* o)
 KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, void* cuda_stream,
                                  kaze_handle** out)
 {
-    if (!out) return KAZE_ERR_INVALID_ARG;
+    if (!out) return create_fail(KAZE_ERR_INVALID_ARG, "null output pointer");
     *out = nullptr;
+    g_create_err.clear();
     kaze_options o;
     if (opt) o = *opt; else kaze_default_options(&o);
     const int N = o.octaves * o.sublevels;
-    if (o.octaves < 1 || o.sublevels < 1 || N > kz::kMaxLevels) return KAZE_ERR_INVALID_ARG;
-    if (!(o.sigma0 > 0.f) || !(o.sigma_d > 0.f)) return KAZE_ERR_INVALID_ARG;
-    if (!(o.k_percentile > 0.0 && o.k_percentile <= 1.0)) return KAZE_ERR_INVALID_ARG;
-    if (o.nbins < 1 || o.nbins > kz::kMaxBins) return KAZE_ERR_INVALID_ARG;
-    if (o.diffusivity != KAZE_G1 && o.diffusivity != KAZE_G2) return KAZE_ERR_INVALID_ARG;
-    if (o.doh_norm != KAZE_DOH_SIGMA4 && o.doh_norm != KAZE_DOH_PAPER_LITERAL) return KAZE_ERR_INVALID_ARG;
-    if (o.max_keypoints < 1) return KAZE_ERR_INVALID_ARG;
-    if (max_w < 3 || max_h < 3 || max_w > 16384 || max_h > 16384) return KAZE_ERR_INVALID_ARG;
-    if (kz::aos_rows_smem_bytes(max_w) == 0 || kz::aos_cols_smem_bytes(max_h) == 0) return KAZE_ERR_INVALID_ARG;
+    if (o.octaves < 1 || o.sublevels < 1 || N > kz::kMaxLevels)
+        return create_fail(KAZE_ERR_INVALID_ARG, "octaves, sublevels must be >= 1 with octaves*sublevels <= 64");
+    if (!(o.sigma0 > 0.f) || !(o.sigma_d > 0.f)) return create_fail(KAZE_ERR_INVALID_ARG, "sigma0 and sigma_d must be > 0");
+    if (!(o.k_percentile > 0.0 && o.k_percentile <= 1.0)) return create_fail(KAZE_ERR_INVALID_ARG, "k_percentile must be in (0, 1]");
+    if (o.nbins < 1 || o.nbins > kz::kMaxBins) return create_fail(KAZE_ERR_INVALID_ARG, "nbins must be in 1..4096");
+    if (o.diffusivity != KAZE_G1 && o.diffusivity != KAZE_G2) return create_fail(KAZE_ERR_INVALID_ARG, "unknown diffusivity");
+    if (o.doh_norm != KAZE_DOH_SIGMA4 && o.doh_norm != KAZE_DOH_PAPER_LITERAL)
+        return create_fail(KAZE_ERR_INVALID_ARG, "unknown doh_norm");
+    if (o.max_keypoints < 1) return create_fail(KAZE_ERR_INVALID_ARG, "max_keypoints must be >= 1");
+    if (max_w < 3 || max_h < 3 || max_w > 16384 || max_h > 16384)
+        return create_fail(KAZE_ERR_INVALID_ARG, "max_w and max_h must be in 3..16384");
+    if (kz::aos_rows_smem_bytes(max_w) == 0 || kz::aos_cols_smem_bytes(max_h) == 0)
+        return create_fail(KAZE_ERR_INVALID_ARG, "image lines too long for the shared-memory line solver");
 
     kaze_handle* h = new (std::nothrow) kaze_handle();
-    if (!h) return KAZE_ERR_OOM;
+    if (!h) return create_fail(KAZE_ERR_OOM, "host allocation failed");
     h->opt = o;
     h->N = N;
     h->max_w = max_w;
@@ -347,7 +366,7 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     h->stream = (cudaStream_t)cuda_stream;
     if (!make_taps(o.sigma0, kz::kMaxGaussR, &h->taps0) || !make_taps(o.sigma_d, kz::kMaxGradR, &h->tapsd)) {
         delete h;
-        return KAZE_ERR_INVALID_ARG;
+        return create_fail(KAZE_ERR_INVALID_ARG, "Gaussian radius too large (sigma0 <= 5.33, sigma_d <= 2)");
     }
     // Eq. 6 (sigma_i = sigma0 2^(o + s/S)) and Eq. 7 (t_i = sigma_i^2 / 2)
     h->tab.n = N;
@@ -370,11 +389,19 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
 
     {
         cudaError_t ce = kz::configure_filter_kernels();
-        if (ce == cudaSuccess) ce = kz::configure_aos_kernels();
-        if (ce == cudaSuccess) ce = kz::configure_detector_kernels();
+        const char* what = "configure_filter_kernels";
+        if (ce == cudaSuccess) {
+            ce = kz::configure_aos_kernels();
+            what = "configure_aos_kernels";
+        }
+        if (ce == cudaSuccess) {
+            ce = kz::configure_detector_kernels();
+            what = "configure_detector_kernels";
+        }
         if (ce != cudaSuccess) {
             delete h;
-            return KAZE_ERR_CUDA;
+            return create_fail(KAZE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(ce) + " " +
+                                                  kz::aos_config_error());
         }
     }
     const size_t pm = (size_t)pitch_for(max_w) * max_h;
@@ -390,11 +417,13 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     const size_t off_hmax = bytes;   bytes += al(sizeof(unsigned int));
     const size_t off_hist = bytes;   bytes += al(sizeof(unsigned int) * o.nbins);
     const size_t off_cnt = bytes;    bytes += al(sizeof(unsigned int));
+    const size_t off_status = bytes; bytes += al(sizeof(int));
     const size_t off_kp = bytes;     bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
     cudaError_t e = cudaMalloc(&h->arena, bytes);
     if (e != cudaSuccess) {
         delete h;
-        return e == cudaErrorMemoryAllocation ? KAZE_ERR_OOM : KAZE_ERR_CUDA;
+        return create_fail(e == cudaErrorMemoryAllocation ? KAZE_ERR_OOM : KAZE_ERR_CUDA,
+                           std::string("cudaMalloc of the device arena: ") + cudaGetErrorName(e));
     }
     char* a = (char*)h->arena;
     h->levels = (float*)(a + off_levels);
@@ -406,14 +435,17 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     h->d_hmax = (unsigned int*)(a + off_hmax);
     h->d_hist = (unsigned int*)(a + off_hist);
     h->d_count = (unsigned int*)(a + off_cnt);
+    h->d_status = (int*)(a + off_status);
     h->d_kp = (kaze_keypoint*)(a + off_kp);
-    e = cudaMallocHost(&h->h_count, sizeof(unsigned int));
+    e = cudaMallocHost(&h->h_count, 2 * sizeof(unsigned int));
     if (e != cudaSuccess) {
         cudaFree(h->arena);
         delete h;
-        return KAZE_ERR_CUDA;
+        return create_fail(KAZE_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorName(e));
     }
     *h->h_count = 0;
+    h->h_status = (int*)(h->h_count + 1);
+    *h->h_status = 0;
     *out = h;
     return KAZE_OK;
 }
@@ -450,7 +482,9 @@ KAZE_API kaze_status kaze_get_contrast(kaze_handle* h, float* k)
     if (!h || !k) return KAZE_ERR_INVALID_ARG;
     if (!h->built) return fail(h, KAZE_ERR_STATE, "no scale space built yet");
     KZ_TRY(h, cudaMemcpyAsync(k, h->d_k, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    KZ_TRY(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     KZ_TRY(h, cudaStreamSynchronize(h->stream));
+    if (*h->h_status) return fail(h, KAZE_ERR_TIMEOUT, "a bounded device-side wait ran out");
     return KAZE_OK;
 }
 
@@ -568,8 +602,12 @@ KAZE_API kaze_status kaze_op_aos_step(kaze_handle* h, const float* d_Lprev, cons
     if (d_Lnext == d_Lprev || d_Lnext == d_g || d_ux == d_Lprev || d_ux == d_g)
         return fail(h, KAZE_ERR_INVALID_ARG, "outputs alias inputs");
     if (!(tau >= 0.f)) return fail(h, KAZE_ERR_INVALID_ARG, "negative tau");
-    KZ_TRY(h, kz::launch_aos_rows(d_Lprev, d_g, d_ux, pitch, w, hh, tau, h->stream));
-    KZ_TRY(h, kz::launch_aos_cols(d_Lprev, d_g, d_ux, d_Lnext, pitch, w, hh, tau, h->stream));
+    KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    KZ_TRY(h, kz::launch_aos_rows(d_Lprev, d_g, d_ux, pitch, w, hh, tau, h->d_status, h->stream));
+    KZ_TRY(h, kz::launch_aos_cols(d_Lprev, d_g, d_ux, d_Lnext, pitch, w, hh, tau, h->d_status, h->stream));
+    KZ_TRY(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    KZ_TRY(h, cudaStreamSynchronize(h->stream));
+    if (*h->h_status) return fail(h, KAZE_ERR_TIMEOUT, "a bounded device-side wait ran out");
     return KAZE_OK;
 }
 
@@ -667,7 +705,7 @@ KAZE_API const char* kaze_status_string(kaze_status s)
 
 KAZE_API const char* kaze_last_error(const kaze_handle* h)
 {
-    if (!h) return "null handle";
+    if (!h) return g_create_err.c_str();
     return h->err.c_str();
 }
 

@@ -40,10 +40,26 @@ __host__ __device__ __forceinline__ int reflect_index(int i, int n)
     return r < n ? r : p - 1 - r;
 }
 
+// Raises a kernel's dynamic shared-memory limit to what the device allows
+// beside the kernel's static shared memory.
+template <typename F>
+inline cudaError_t allow_max_dynamic_smem(F* func)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)func);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 // Raise every kernel's dynamic shared-memory limit once (outside any stream
 // capture); launches then pass their actual size.
 cudaError_t configure_filter_kernels();
 cudaError_t configure_aos_kernels();
+const char* aos_config_error();  // why configure_aos_kernels failed, if it did
 cudaError_t configure_detector_kernels();
 
 // ---- launchers (all asynchronous on `st`; return the launch error) ----
@@ -68,10 +84,12 @@ cudaError_t launch_percentile(const unsigned int* d_hist, int nbins,
 cudaError_t launch_set_scalar(float* d_dst, float value, cudaStream_t st);
 
 // AOS step of Eq. 4: rows (writes ux), then columns + average (writes Lnext).
+// Rows need 16-byte aligned rows (pitch % 4 == 0); columns are staged by TMA
+// tensor copies.  A bounded wait that runs out sets bit 0 of *d_status.
 cudaError_t launch_aos_rows(const float* L, const float* g, float* ux, int pitch,
-                            int w, int h, float tau, cudaStream_t st);
+                            int w, int h, float tau, int* d_status, cudaStream_t st);
 cudaError_t launch_aos_cols(const float* L, const float* g, const float* ux, float* Lnext,
-                            int pitch, int w, int h, float tau, cudaStream_t st);
+                            int pitch, int w, int h, float tau, int* d_status, cudaStream_t st);
 size_t aos_rows_smem_bytes(int w);
 size_t aos_cols_smem_bytes(int h);
 

@@ -173,7 +173,8 @@ class Kaze:
         st = self._L.kaze_create(ctypes.byref(opt), int(max_w), int(max_h),
                                  _vp(stream.cuda_stream), ctypes.byref(h))
         if st != OK:
-            raise KazeError(st, f"kaze_create failed: {self._L.kaze_status_string(st).decode()}")
+            raise KazeError(st, f"kaze_create failed: {self._L.kaze_status_string(st).decode()}: "
+                                f"{self._L.kaze_last_error(None).decode()}")
         self._h = h
         self.max_w, self.max_h = int(max_w), int(max_h)
         self.n_levels = opt.octaves * opt.sublevels
