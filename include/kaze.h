@@ -90,8 +90,9 @@ typedef struct kaze_handle kaze_handle;
 /* Fills *opt with the defaults listed beside each field. */
 void kaze_default_options(kaze_options* opt);
 
-/* Creates a handle for images up to max_w x max_h (3 <= max_w <= 16384,
- * 3 <= max_h <= 6144: a column strip must fit in shared memory).
+/* Creates a handle for images up to max_w x max_h (3 <= max_w, max_h <= 4128:
+ * each row and column is solved by 32 chunks whose coefficients must fit in
+ * registers and shared memory).
  * Allocates all device buffers up front (about (2N + 3) * max_w * max_h * 4
  * bytes).  cuda_stream: the cudaStream_t all work goes to.  On error *out is
  * NULL.  Errors: INVALID_ARG (bad options or sizes), OOM, CUDA. */
@@ -180,7 +181,9 @@ kaze_status kaze_op_doh(kaze_handle* h, const float* d_L, float* d_D, int pitch,
 
 /* Extrema of a caller-supplied response stack of n levels (level l at
  * d_D + l * plane_stride, each with the given pitch); level l has scale
- * sigma[l] (host array).  Output as kaze_find_extrema.  Synchronises. */
+ * sigma[l] (host array).  d_D must be 16-byte aligned and pitch and
+ * plane_stride multiples of 4 (rows are read 4 values at a time).  Output as
+ * kaze_find_extrema.  Synchronises. */
 kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch, long long plane_stride,
                             int w, int h_, int n, const float* h_sigma,
                             kaze_keypoint* h_out, int capacity, int* count);

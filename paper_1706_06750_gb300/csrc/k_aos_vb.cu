@@ -1,0 +1,9 @@
+// k_aos_vb.cu -- instantiates one group of the AOS line-solver
+// variants (aos_solver.cuh) so the groups compile in parallel.
+#include "aos_solver.cuh"
+
+namespace kz {
+namespace aos {
+KZ_AOS_VARIANTS_B(KZ_AOS_INSTANTIATE)
+}  // namespace aos
+}  // namespace kz

@@ -71,6 +71,8 @@ enum GradMode { MODE_COND = 0, MODE_MAX = 1, MODE_HIST = 2 };
 // transpose).  MODE_COND writes the conductance g of Eq. 3; MODE_MAX folds
 // |grad| of interior pixels into a global maximum; MODE_HIST bins the
 // non-zero interior magnitudes.
+// Every pass works on runs of 4 consecutive outputs per thread so each
+// shared-memory value loaded feeds several taps from registers.
 template <int MODE, int R>
 __global__ void __launch_bounds__(BX* BY)
 k_gradient(const float* __restrict__ L, float* __restrict__ g, int pitch, int w, int h,
@@ -80,16 +82,19 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, int pitch, int w,
     constexpr int CW = TX + 2, CH = TY + 2;      // smoothed region (halo 1 for Scharr)
     constexpr int SW = CW + 2 * R, SH = CH + 2 * R;
     constexpr int KX = (SW + BX - 1) / BX;
-    __shared__ float A[SH][SW + 1];  // raw L
-    __shared__ float B[SH][CW + 1];  // row-smoothed
-    __shared__ float C[CH][CW + 1];  // smoothed
+    constexpr int CWR = (CW + 3) / 4;            // 4-wide runs per row of B / C
+    constexpr int CHR = (CH + 3) / 4;            // 4-high runs per column of C
+    __shared__ float A[SH][SW + 4];  // raw L (+4: runs may read past the edge)
+    __shared__ float B[SH + 4][CW + 4];  // row-smoothed
+    __shared__ float C[CH + 4][CW + 1];  // smoothed
     extern __shared__ unsigned int hist_s[];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * BX + tx;
+    constexpr int NT = BX * BY;
 
     if (MODE == MODE_HIST) {
-        for (int i = tid; i < nbins; i += BX * BY) hist_s[i] = 0u;
+        for (int i = tid; i < nbins; i += NT) hist_s[i] = 0u;
     }
     int gx[KX];
 #pragma unroll
@@ -102,31 +107,35 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, int pitch, int w,
             if (tx + k * BX < SW) A[sy][tx + k * BX] = __ldg(row + gx[k]);
     }
     __syncthreads();
+    // rows: B[sy][4u .. 4u+3]
 #pragma unroll
-    for (int sy = ty; sy < SH; sy += BY) {
+    for (int t = tid; t < SH * CWR; t += NT) {
+        const int sy = t / CWR, u = t - sy * CWR;
+        float v[4 + 2 * R];
 #pragma unroll
-        for (int k = 0; k < (CW + BX - 1) / BX; ++k) {
-            const int sx = tx + k * BX;
-            if (sx < CW) {
-                float acc = 0.f;
+        for (int j = 0; j < 4 + 2 * R; ++j) v[j] = A[sy][4 * u + j];
 #pragma unroll
-                for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], A[sy][sx + j], acc);
-                B[sy][sx] = acc;
-            }
+        for (int q = 0; q < 4; ++q) {
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], v[q + j], acc);
+            B[sy][4 * u + q] = acc;
         }
     }
     __syncthreads();
+    // columns: C[4u .. 4u+3][sx]
 #pragma unroll
-    for (int sy = ty; sy < CH; sy += BY) {
+    for (int t = tid; t < CW * CHR; t += NT) {
+        const int u = t / CW, sx = t - u * CW;
+        float v[4 + 2 * R];
 #pragma unroll
-        for (int k = 0; k < (CW + BX - 1) / BX; ++k) {
-            const int sx = tx + k * BX;
-            if (sx < CW) {
-                float acc = 0.f;
+        for (int j = 0; j < 4 + 2 * R; ++j) v[j] = B[4 * u + j][sx];
 #pragma unroll
-                for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], B[sy + j][sx], acc);
-                C[sy][sx] = acc;
-            }
+        for (int q = 0; q < 4; ++q) {
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], v[q + j], acc);
+            C[4 * u + q][sx] = acc;
         }
     }
     __syncthreads();
@@ -137,22 +146,28 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, int pitch, int w,
     float local_max = 0.f;
     const float c0 = 3.f / 16.f, c1 = 10.f / 16.f;
     const int gxo = x0 + tx;
-
+    const int oy0 = 4 * ty;  // this thread's 4 output rows
+    // C[cy][cx] holds the smoothed value at (x0 - 1 + cx, y0 - 1 + cy)
+    float cm[6], cc[6], cp[6];
 #pragma unroll
-    for (int oy = ty; oy < TY; oy += BY) {
-        const int gy = y0 + oy;
-        // C[cy][cx] holds the smoothed value at (x0 - 1 + cx, y0 - 1 + cy)
-        const int cy = oy + 1, cx = tx + 1;
-        float lx = c0 * 0.5f * (C[cy - 1][cx + 1] - C[cy - 1][cx - 1]);
-        lx += c1 * 0.5f * (C[cy][cx + 1] - C[cy][cx - 1]);
-        lx += c0 * 0.5f * (C[cy + 1][cx + 1] - C[cy + 1][cx - 1]);
-        float ly = c0 * 0.5f * (C[cy + 1][cx - 1] - C[cy - 1][cx - 1]);
-        ly += c1 * 0.5f * (C[cy + 1][cx] - C[cy - 1][cx]);
-        ly += c0 * 0.5f * (C[cy + 1][cx + 1] - C[cy - 1][cx + 1]);
+    for (int j = 0; j < 6; ++j) {
+        cm[j] = C[oy0 + j][tx];
+        cc[j] = C[oy0 + j][tx + 1];
+        cp[j] = C[oy0 + j][tx + 2];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int gy = y0 + oy0 + q;
+        float lx = c0 * 0.5f * (cp[q] - cm[q]);
+        lx += c1 * 0.5f * (cp[q + 1] - cm[q + 1]);
+        lx += c0 * 0.5f * (cp[q + 2] - cm[q + 2]);
+        float ly = c0 * 0.5f * (cm[q + 2] - cm[q]);
+        ly += c1 * 0.5f * (cc[q + 2] - cc[q]);
+        ly += c0 * 0.5f * (cp[q + 2] - cp[q]);
         if (gxo >= w || gy >= h) continue;
         if (MODE == MODE_COND) {
-            const float q = (lx * lx + ly * ly) / (kk * kk);
-            g[(size_t)gy * pitch + gxo] = diffusivity == KAZE_G1 ? expf(-q) : 1.f / (1.f + q);
+            const float qv = (lx * lx + ly * ly) / (kk * kk);
+            g[(size_t)gy * pitch + gxo] = diffusivity == KAZE_G1 ? expf(-qv) : 1.f / (1.f + qv);
         } else {
             const bool interior = gxo >= 1 && gxo <= w - 2 && gy >= 1 && gy <= h - 2;
             if (!interior) continue;
@@ -173,7 +188,7 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, int pitch, int w,
     }
     if (MODE == MODE_HIST) {
         __syncthreads();
-        for (int i = tid; i < nbins; i += BX * BY) {
+        for (int i = tid; i < nbins; i += NT) {
             const unsigned int v = hist_s[i];
             if (v) atomicAdd(&d_hist[i], v);
         }

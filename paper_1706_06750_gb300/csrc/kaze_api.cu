@@ -641,6 +641,8 @@ KAZE_API kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch
     KZ_CHECK(check_image(h, w, hh));
     if (pitch < w || plane_stride < (long long)pitch * hh || n < 1 || n > kz::kMaxLevels)
         return fail(h, KAZE_ERR_INVALID_ARG, "bad pitch, plane stride or level count");
+    if (pitch % 4 || plane_stride % 4 || ((uintptr_t)d_D & 15))
+        return fail(h, KAZE_ERR_INVALID_ARG, "responses must be 16-byte aligned with pitch and plane stride % 4 == 0");
     kz::LevelTable t = h->tab;
     t.n = n;
     for (int i = 0; i < n; ++i) t.sigma[i] = h_sigma[i];
