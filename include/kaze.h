@@ -188,6 +188,31 @@ kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch, long lo
                             int w, int h_, int n, const float* h_sigma,
                             kaze_keypoint* h_out, int capacity, int* count);
 
+/* ---- a step that allocates nothing ------------------------------------- *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot let a library allocate device memory (a framework whose
+ * caching allocator owns the GPU's memory, a processing loop that must not
+ * allocate once running).
+ *
+ * kaze_aos_step_static computes d_Lnext from d_Lprev and the conductance
+ * d_g exactly as kaze_op_aos_step does (one AOS step of Eq. 4 with step
+ * tau), without a handle and without allocating: the row solution it needs
+ * internally lives in a file-scope device array that every GPU loading the
+ * library holds until the process exits.  Limits: pitch * h <= 4,194,304
+ * (16 MiB of scratch), 3 <= w, h <= 4128, pitch >= w and a multiple of 4,
+ * all three buffers 16-byte aligned, d_Lnext distinct from the inputs;
+ * anything else returns KAZE_ERR_INVALID_ARG before touching the GPU.
+ * The first call on a device looks up the array's device address and sets
+ * the kernels' shared-memory limits for the current device, so make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (different streams, or another thread)
+ * race on it and must be serialised by the caller.  Work goes to
+ * cuda_stream (cudaStream_t); the call waits for it and returns
+ * KAZE_ERR_TIMEOUT if a bounded device wait ran out, KAZE_ERR_CUDA on a
+ * CUDA failure. */
+kaze_status kaze_aos_step_static(const float* d_Lprev, const float* d_g, float* d_Lnext, int pitch, int w,
+                                 int h_, float tau, void* cuda_stream);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Number of kernel kinds the pipeline launches, and the name of kind k

@@ -92,6 +92,7 @@ _SIGNATURES = {
     "kaze_op_doh": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _i]),
     "kaze_op_extrema": (_i, [_vp, _vp, _i, ctypes.c_longlong, _i, _i, _i, ctypes.POINTER(_f),
                              ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
+    "kaze_aos_step_static": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _vp]),
     "kaze_kernel_kinds": (_i, []),
     "kaze_kernel_name": (ctypes.c_char_p, [_i]),
     "kaze_last_launch_count": (_i, [_vp]),
@@ -130,6 +131,20 @@ def default_options(**overrides) -> Options:
     for k, v in overrides.items():
         setattr(o, k, v)
     return o
+
+
+def aos_step_static(Lprev, g, Lnext, tau, stream=None):
+    """One AOS step with no allocation (kaze_aos_step_static): for callers
+    that cannot let the library allocate device memory.  Lprev, g, Lnext are
+    2-D float32 CUDA tensors sharing one row pitch; returns the status code."""
+    import torch
+    w, h, pitch = _check_image(Lprev)
+    for t in (g, Lnext):
+        if _check_image(t) != (w, h, pitch):
+            raise KazeError(ERR_INVALID_ARG, "Lprev, g and Lnext must share shape and pitch")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(lib().kaze_aos_step_static(_vp(Lprev.data_ptr()), _vp(g.data_ptr()), _vp(Lnext.data_ptr()),
+                                          pitch, w, h, float(tau), _vp(s.cuda_stream)))
 
 
 class _DeviceView:
