@@ -13,7 +13,7 @@
  *   R2 Gaussian: sampled, normalised, radius ceil(3 sigma).
  *   R3 Eq. 6 prints 2^((o+s)/S); read as sigma0 * 2^(o + s/S) (octaves double
  *      sigma, no two levels coincide).  N = O*S levels, indices 0..N-1.
- *   R4 k (Sec. III-1, "gradient histogram ... automatic procedure"): smooth
+ *   R4 k (Sec. III-1 takes k from a gradient histogram, procedure not given): smooth
  *      L0 with G(sigma_d = 1), 3x3 Scharr, magnitude over interior pixels,
  *      hmax = max, histogram of the non-zero magnitudes in nbins bins,
  *      k = hmax * (b+1)/nbins for the smallest bin b whose cumulative count
