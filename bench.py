@@ -307,6 +307,9 @@ def run_ours(args, rank, world, local_rank):
     achieved = kernels[dom]["algorithmic_gbs"]
     traffic = ncu_traffic(dom)
 
+    batched = None if args.no_batch else run_batched(args, kaze, synth, torch, stream, world, rank,
+                                                        max_over_ranks, barrier)
+
     if dist is not None:
         dist.barrier()
     if rank != 0:
@@ -340,6 +343,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes},
         "kernels": kernels,
+        "batched": batched,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -347,6 +351,55 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
     k.close()
     return 0
+
+
+def run_batched(args, kaze, synth, torch, stream, world, rank, max_over_ranks, barrier):
+    """64 mixed-size images (each rank its own set): the batched persistent
+    path (autotuned solve tiles, cached) against the plain single-image path
+    run image after image.  The 64 inputs (~360 MB) exceed L2."""
+    sizes = synth.batch_sizes(64, seed=4000 + 100 * rank)
+    imgs = [torch.from_numpy(a).cuda() for a in synth.batch_images(64, seed=4000 + 100 * rank)]
+    mpx = sum(w * h for w, h in sizes) / 1e6
+    reps = max(2, min(args.steps, 10))
+    cache = os.path.join(ROOT, "paper_1706_06750_gb300", "_build", "batch_tuning.json")
+    with kaze.Batch(sizes) as b:
+        tuning, tune_ms = b.autotune(imgs, reps=2, cache=cache)
+        for _ in range(2):
+            b.detect(imgs)
+        launches = 1
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(b.stream):
+            ev[0].record(b.stream)
+            for _ in range(reps):
+                b.detect(imgs)
+            ev[1].record(b.stream)
+        torch.cuda.synchronize()
+        t_batch = max_over_ranks(ev[0].elapsed_time(ev[1]))
+        counts = [len(k) for k in b.detect(imgs)]
+    mw = max(w for w, _ in sizes)
+    mh = max(h for _, h in sizes)
+    with kaze.Kaze(mw, mh) as k:
+        for x in imgs[:4]:
+            k.detect(x)
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(k.stream):
+            ev[0].record(k.stream)
+            for x in imgs:
+                k.detect(x)
+            ev[1].record(k.stream)
+        torch.cuda.synchronize()
+        t_plain = max_over_ranks(ev[0].elapsed_time(ev[1]))
+    img_s = world * 64 * reps / (t_batch * 1e-3)
+    plain_s = world * 64 / (t_plain * 1e-3)
+    return {"images": 64, "megapixels": round(mpx, 3), "img_per_s": img_s,
+            "mpix_per_s": img_s * mpx / 64, "ms_per_batch": t_batch / reps,
+            "plain_img_per_s": plain_s, "plain_ms_per_64": t_plain,
+            "speedup_vs_plain": img_s / plain_s, "tuning": list(tuning),
+            "autotune_best_ms": tune_ms, "keypoints": int(sum(counts)),
+            "launches_per_batch": launches,
+            "note": "one persistent kernel per batch; plain = kaze_detect image after image"}
 
 
 def main():
@@ -357,6 +410,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = env_int("RANK", 0)

@@ -188,6 +188,68 @@ kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch, long lo
                             int w, int h_, int n, const float* h_sigma,
                             kaze_keypoint* h_out, int capacity, int* count);
 
+/* ---- batches of images: one persistent launch -------------------------- *
+ * A batch handle serves a fixed list of n images of (possibly different)
+ * sizes w[i] x h[i] (3..4096 each), all with the same options.  One call
+ * runs the whole detection of every image -- presmoothing, contrast
+ * factor, the N-1 AOS steps, the responses of all levels and the extrema --
+ * as ONE persistent kernel whose CTAs pop work items (tiles, row groups,
+ * column strips) from an ordered device queue; an item waits, with a
+ * bounded spin, until the stages it reads are complete for its image.  The
+ * launch and its set-up are recorded once as a CUDA graph and replayed
+ * (except on the legacy or per-thread default stream).  Results match the
+ * single-image path. */
+typedef struct kaze_batch kaze_batch;
+
+/* Solve-tile shape of the batched kernel: columns per column-solve strip
+ * (4: 64 chunks per column, 8: 32 chunks) and persistent CTAs per SM (1 or
+ * more; capped by occupancy). */
+typedef struct kaze_batch_tuning {
+    int cols_per_strip;
+    int ctas_per_sm;
+} kaze_batch_tuning;
+
+/* Allocates every plane of every image (2N + 2 planes each), the keypoint
+ * buffers (max_keypoints per image) and the work list.  Errors:
+ * INVALID_ARG (options, n outside 1..65535, sizes), OOM, CUDA. */
+kaze_status kaze_batch_create(const kaze_options* opt, int n, const int* w, const int* h_, void* cuda_stream,
+                              kaze_batch** out);
+
+/* Detects keypoints in the n device images d_imgs[i] (row pitch pitches[i]
+ * elements, or w[i] when pitches is NULL).  Image i's keypoints, sorted by
+ * (level, iy, ix), go to h_out + i * capacity_per_image and their true
+ * number to counts[i]; KAZE_ERR_CAPACITY if any image had more than fit.
+ * KAZE_ERR_TIMEOUT if a bounded device wait ran out.  Synchronises. */
+kaze_status kaze_batch_detect(kaze_batch* b, const float* const* d_imgs, const int* pitches,
+                              kaze_keypoint* h_out, int capacity_per_image, int* counts);
+
+/* Borrowed pointers to level / response `level` of image `image` after the
+ * last kaze_batch_detect, with their pitch. */
+kaze_status kaze_batch_get_level(kaze_batch* b, int image, int level, const float** d_level, int* pitch_elems);
+kaze_status kaze_batch_get_response(kaze_batch* b, int image, int level, const float** d_doh, int* pitch_elems);
+
+/* Current / new solve-tile shape (a new shape re-plans and re-records). */
+kaze_status kaze_batch_get_tuning(const kaze_batch* b, kaze_batch_tuning* t);
+kaze_status kaze_batch_set_tuning(kaze_batch* b, const kaze_batch_tuning* t);
+
+/* Autotuner: times every candidate shape (cols_per_strip in {4, 8} x
+ * ctas_per_sm in {1, 2}) on the given images, `reps` runs each (CUDA
+ * events), keeps the fastest and reports it and its mean time in ms. */
+kaze_status kaze_batch_autotune(kaze_batch* b, const float* const* d_imgs, const int* pitches, int reps,
+                                kaze_batch_tuning* best, double* best_ms);
+
+/* Test hook for failure detection: sets how many SM cycles a device-side
+ * wait may take (default 2^31) and, if stall_image >= 0, makes one stage
+ * of that image wait for an item that never exists, so the wait runs out
+ * and kaze_batch_detect returns KAZE_ERR_TIMEOUT.  stall_image < 0 clears
+ * the hook. */
+kaze_status kaze_batch_set_wait_limit(kaze_batch* b, long long cycles, int stall_image);
+
+/* Message of the batch's first error ("" if none). */
+const char* kaze_batch_last_error(const kaze_batch* b);
+
+void kaze_batch_destroy(kaze_batch* b);
+
 /* ---- a step that allocates nothing ------------------------------------- *
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot let a library allocate device memory (a framework whose

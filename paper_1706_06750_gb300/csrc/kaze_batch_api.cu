@@ -1,0 +1,528 @@
+// kaze_batch_api.cu -- host runtime of the batched detection: one handle for
+// a fixed set of image sizes, its device arena, the ordered work list of the
+// persistent kernel (k_batch.cu), the captured CUDA graph around it and the
+// autotuner of its solve-tile shapes.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kaze_batch.h"
+
+#define KAZE_API extern "C" __attribute__((visibility("default")))
+
+using kz::batch::ImageDesc;
+using kz::batch::Item;
+
+struct kaze_batch {
+    kaze_options opt;
+    int n = 0, N = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<int> w, h, pitch;
+    std::vector<long long> plane;
+
+    void* arena = nullptr;           // device: planes, scratch, statistics, keypoints
+    ImageDesc* d_desc = nullptr;     // device descriptors
+    ImageDesc* h_desc = nullptr;     // pinned host copy (image pointers updated per call)
+    unsigned* d_count_status = nullptr;  // per-image keypoint counts then status word (device)
+    unsigned* h_count_status = nullptr;  // pinned host copy
+    unsigned* d_next = nullptr;
+    unsigned* d_done = nullptr;
+    unsigned* d_need = nullptr;
+    Item* d_items = nullptr;
+    size_t items_cap = 0;
+    void* stats_base = nullptr;      // per-image k / hmax / hist block, cleared per call
+    size_t stats_bytes = 0;
+
+    kz::batch::BatchParams params;
+    kaze_batch_tuning tuning{4, 2};
+    int grid = 0, smem = 0;
+    int n_items = 0;
+    long long spin_limit = 1ll << 31;
+    int stall_image = -1;            // test hook: a stage that never completes
+
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<kaze_keypoint> hkp;
+    std::string err;
+};
+
+namespace {
+
+kaze_status bfail(kaze_batch* b, kaze_status s, const std::string& m)
+{
+    if (b && b->err.empty()) b->err = m;
+    return s;
+}
+
+#define KB_TRY(b, call)                                                                                  \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return bfail((b), KAZE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorName(e_));          \
+    } while (0)
+
+int odd_chunk(int n, int P)
+{
+    int m = (n + P - 1) / P;
+    m |= 1;
+    return m < 3 ? 3 : m;
+}
+
+bool make_taps(double sigma, int rmax, kz::GaussTaps* t)
+{
+    int r = (int)std::ceil(3.0 * sigma);
+    if (r < 1) r = 1;
+    if (r > rmax) return false;
+    double w[2 * kz::kMaxGaussR + 1], sum = 0.0;
+    for (int j = -r; j <= r; ++j) {
+        w[j + r] = std::exp(-(double)j * j / (2.0 * sigma * sigma));
+        sum += w[j + r];
+    }
+    t->r = r;
+    for (int j = 0; j <= 2 * r; ++j) t->w[j] = (float)(w[j] / sum);
+    return true;
+}
+
+// Shared memory the persistent kernel needs for the batch's largest item.
+int pool_floats(const kaze_batch* b, int cols)
+{
+    using namespace kz::batch;
+    size_t need = 0;
+    const int r0 = b->params.taps0.r, rd = b->params.tapsd.r;
+    need = std::max(need, (size_t)(32 + 2 * r0) * (32 + 2 * r0) + (size_t)(32 + 2 * r0) * 32);
+    need = std::max(need, (size_t)(34 + 2 * rd) * (34 + 2 * rd) + (size_t)(34 + 2 * rd) * 34 + 34 * 34 +
+                              (size_t)b->opt.nbins);
+    int smax = 1;
+    for (int i = 0; i < b->N; ++i) smax = std::max(smax, b->params.tab.step[i]);
+    need = std::max(need, (size_t)(64 + 4 * smax) * ((64 + 4 * smax) | 1));
+    for (int i = 0; i < b->n; ++i) {
+        const int ls = (64 * odd_chunk(b->w[i], 64) + 3) / 4 * 4;
+        need = std::max(need, (size_t)4 * (3 * ls + 8 * 64));
+        const int P = kBatchThreads / cols;
+        const int rs = P * odd_chunk(b->h[i], P);
+        need = std::max(need, (size_t)3 * rs * cols + (size_t)8 * P * cols);
+    }
+    return (int)need;
+}
+
+// The ordered work list (stage-major across images) and the per-stage
+// item counts.
+void build_items(const kaze_batch* b, int cols, std::vector<Item>& items, std::vector<unsigned>& need)
+{
+    using namespace kz::batch;
+    const int S = slots_per_image();
+    need.assign((size_t)b->n * S, 0u);
+    items.clear();
+    auto add = [&](ItemKind kind, int level, int img, unsigned count, int slot) {
+        for (unsigned t = 0; t < count; ++t) items.push_back(Item{(uint8_t)kind, (uint8_t)level, (uint16_t)img, t});
+        need[(size_t)img * S + slot] += count;
+    };
+    auto t32 = [&](int i) { return (unsigned)(((b->w[i] + 31) / 32) * ((b->h[i] + 31) / 32)); };
+    auto t64 = [&](int i) { return (unsigned)(((b->w[i] + 63) / 64) * ((b->h[i] + 63) / 64)); };
+    for (int i = 0; i < b->n; ++i) add(IT_PRESMOOTH, 0, i, t32(i), slot_presmooth());
+    for (int i = 0; i < b->n; ++i) add(IT_GMAX, 0, i, t32(i), slot_gmax());
+    for (int i = 0; i < b->n; ++i) add(IT_GHIST, 0, i, t32(i), slot_ghist());
+    for (int i = 0; i < b->n; ++i) add(IT_PCT, 0, i, 1, slot_pct());
+    for (int i = 0; i < b->n; ++i) add(IT_DOH, 0, i, t64(i), slot_doh(0));
+    for (int l = 1; l < b->N; ++l) {
+        for (int i = 0; i < b->n; ++i) add(IT_COND, l, i, t32(i), slot_cond(l));
+        for (int i = 0; i < b->n; ++i) add(IT_ROWS, l, i, (unsigned)((b->h[i] + 3) / 4), slot_rows(l));
+        for (int i = 0; i < b->n; ++i) add(IT_COLS, l, i, (unsigned)((b->w[i] + cols - 1) / cols), slot_cols(l));
+        for (int i = 0; i < b->n; ++i) add(IT_DOH, l, i, t64(i), slot_doh(l));
+        if (l >= 2)
+            for (int i = 0; i < b->n; ++i)
+                add(IT_EXTREMA, l - 1, i, (unsigned)((b->h[i] + kExtremaRows - 1) / kExtremaRows),
+                    slot_extrema(l - 1));
+    }
+}
+
+void drop_graph(kaze_batch* b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+}
+
+// Prepares the work list, shared memory and grid for the current tuning.
+kaze_status prepare(kaze_batch* b)
+{
+    using namespace kz::batch;
+    const int cols = b->tuning.cols_per_strip;
+    std::vector<Item> items;
+    std::vector<unsigned> need;
+    build_items(b, cols, items, need);
+    if (b->stall_image >= 0 && b->stall_image < b->n)  // test hook: unreachable count
+        need[(size_t)b->stall_image * slots_per_image() + slot_rows(1)] += 1;
+    if (items.size() > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        KB_TRY(b, cudaMalloc(&b->d_items, sizeof(Item) * items.size()));
+        b->items_cap = items.size();
+    }
+    KB_TRY(b, cudaMemcpy(b->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice));
+    KB_TRY(b, cudaMemcpy(b->d_need, need.data(), sizeof(unsigned) * need.size(), cudaMemcpyHostToDevice));
+    b->n_items = (int)items.size();
+    b->smem = pool_floats(b, cols) * (int)sizeof(float);
+    int optin = 0, dev = 0;
+    KB_TRY(b, cudaGetDevice(&dev));
+    KB_TRY(b, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (b->smem + 64 > optin) return bfail(b, KAZE_ERR_INVALID_ARG, "images too large for the batched kernel");
+    KB_TRY(b, configure_batch_kernel(b->smem));
+    int per_sm = 0, sms = 0;
+    KB_TRY(b, batch_occupancy(b->smem, &per_sm));
+    KB_TRY(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) return bfail(b, KAZE_ERR_INVALID_ARG, "batched kernel does not fit on an SM");
+    b->grid = sms * std::min(per_sm, std::max(1, b->tuning.ctas_per_sm));
+    b->params.items = b->d_items;
+    b->params.n_items = b->n_items;
+    b->params.cols = cols;
+    b->params.spin_limit = b->spin_limit;
+    drop_graph(b);
+    return KAZE_OK;
+}
+
+kaze_status enqueue(kaze_batch* b)
+{
+    using namespace kz::batch;
+    cudaStream_t st = b->stream;
+    KB_TRY(b, cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), st));
+    KB_TRY(b, cudaMemsetAsync(b->d_done, 0, sizeof(unsigned) * (size_t)b->n * slots_per_image(), st));
+    KB_TRY(b, cudaMemsetAsync(b->d_count_status, 0, sizeof(unsigned) * (b->n + 1), st));
+    KB_TRY(b, cudaMemsetAsync(b->stats_base, 0, b->stats_bytes, st));
+    KB_TRY(b, cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(ImageDesc) * b->n, cudaMemcpyHostToDevice, st));
+    KB_TRY(b, launch_batch(b->params, b->grid, b->smem, st));
+    KB_TRY(b, cudaMemcpyAsync(b->h_count_status, b->d_count_status, sizeof(unsigned) * (b->n + 1),
+                              cudaMemcpyDeviceToHost, st));
+    return KAZE_OK;
+}
+
+kaze_status run(kaze_batch* b)
+{
+    const bool capturable = b->stream && b->stream != cudaStreamLegacy && b->stream != cudaStreamPerThread;
+    if (!capturable) return enqueue(b);
+    if (!b->gexec) {
+        cudaGraph_t graph = nullptr;
+        KB_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        const kaze_status s = enqueue(b);
+        const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (s != KAZE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return bfail(b, KAZE_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorName(e));
+        const cudaError_t ei = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            b->gexec = nullptr;
+            return bfail(b, KAZE_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorName(ei));
+        }
+    }
+    KB_TRY(b, cudaGraphLaunch(b->gexec, b->stream));
+    return KAZE_OK;
+}
+
+kaze_status set_inputs(kaze_batch* b, const float* const* d_imgs, const int* pitches)
+{
+    if (!d_imgs) return bfail(b, KAZE_ERR_INVALID_ARG, "null image list");
+    for (int i = 0; i < b->n; ++i) {
+        const int p = pitches ? pitches[i] : b->w[i];
+        if (!d_imgs[i] || p < b->w[i]) return bfail(b, KAZE_ERR_INVALID_ARG, "bad image pointer or pitch");
+        b->h_desc[i].img = d_imgs[i];
+        b->h_desc[i].img_pitch = p;
+    }
+    return KAZE_OK;
+}
+
+}  // namespace
+
+KAZE_API kaze_status kaze_batch_create(const kaze_options* opt, int n, const int* w, const int* h, void* cuda_stream,
+                                       kaze_batch** out)
+{
+    using namespace kz::batch;
+    if (!out || !w || !h || n < 1 || n > 65535) return KAZE_ERR_INVALID_ARG;
+    *out = nullptr;
+    kaze_options o;
+    if (opt) o = *opt; else kaze_default_options(&o);
+    const int N = o.octaves * o.sublevels;
+    if (o.octaves < 1 || o.sublevels < 1 || N > kz::kMaxLevels || N > 255) return KAZE_ERR_INVALID_ARG;
+    if (!(o.sigma0 > 0.f) || !(o.sigma_d > 0.f) || !(o.k_percentile > 0.0 && o.k_percentile <= 1.0))
+        return KAZE_ERR_INVALID_ARG;
+    if (o.nbins < 1 || o.nbins > kz::kMaxBins || o.max_keypoints < 1) return KAZE_ERR_INVALID_ARG;
+    if (o.diffusivity != KAZE_G1 && o.diffusivity != KAZE_G2) return KAZE_ERR_INVALID_ARG;
+    if (o.doh_norm != KAZE_DOH_SIGMA4 && o.doh_norm != KAZE_DOH_PAPER_LITERAL) return KAZE_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (w[i] < 3 || h[i] < 3 || w[i] > 4096 || h[i] > 4096) return KAZE_ERR_INVALID_ARG;
+
+    kaze_batch* b = new (std::nothrow) kaze_batch();
+    if (!b) return KAZE_ERR_OOM;
+    b->opt = o;
+    b->n = n;
+    b->N = N;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->w.assign(w, w + n);
+    b->h.assign(h, h + n);
+    BatchParams& P = b->params;
+    std::memset(&P, 0, sizeof(P));
+    if (!make_taps(o.sigma0, kz::kMaxGaussR, &P.taps0) || !make_taps(o.sigma_d, kz::kMaxGradR, &P.tapsd)) {
+        delete b;
+        return KAZE_ERR_INVALID_ARG;
+    }
+    // Eq. 6-8: scales, evolution steps, derivative steps and normalisation
+    double sig[kz::kMaxLevels], t[kz::kMaxLevels];
+    P.tab.n = N;
+    P.tab.sublevels = o.sublevels;
+    for (int oc = 0; oc < o.octaves; ++oc)
+        for (int s = 0; s < o.sublevels; ++s) {
+            const int i = oc * o.sublevels + s;
+            sig[i] = (double)o.sigma0 * std::pow(2.0, (double)oc + (double)s / o.sublevels);
+            t[i] = 0.5 * sig[i] * sig[i];
+            int st = (int)std::floor(sig[i] + 0.5);
+            st = st < 1 ? 1 : st;
+            P.tab.step[i] = st;
+            P.tab.sigma[i] = (float)sig[i];
+            double norm;
+            if (o.doh_norm == KAZE_DOH_PAPER_LITERAL) {
+                const double kn = sig[i] / std::pow(2.0, (double)oc);
+                norm = kn * kn;
+            } else {
+                norm = (double)st * st * st * st;
+            }
+            P.tab.norm[i] = (float)norm;
+            const double d = 1024.0 * st * st;
+            P.doh_scale[i] = (float)(norm / (d * d));
+            P.tau[i] = i > 0 ? (float)(t[i] - t[i - 1]) : 0.f;
+        }
+    P.pct = o.k_percentile;
+    P.nbins = o.nbins;
+    P.diffusivity = o.diffusivity;
+    P.thr = o.dthreshold;
+    P.edge_r = o.edge_r;
+    P.k_override = o.k_override;
+    P.N = N;
+    P.slots = slots_per_image();
+
+    // arena: per image N levels, N responses, g, ux; then statistics, keypoints
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    size_t planes = 0;
+    b->pitch.resize(n);
+    b->plane.resize(n);
+    for (int i = 0; i < n; ++i) {
+        b->pitch[i] = (w[i] + 31) / 32 * 32;
+        b->plane[i] = (long long)b->pitch[i] * h[i];
+        planes += al(sizeof(float) * (size_t)b->plane[i] * (2 * N + 2));
+    }
+    const size_t stat_per = al(sizeof(float)) + al(sizeof(unsigned)) + al(sizeof(unsigned) * o.nbins);
+    b->stats_bytes = stat_per * n;
+    const size_t kp_bytes = al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints) * n;
+    const size_t ctl = al(sizeof(ImageDesc) * n) + al(sizeof(unsigned) * (n + 1)) + al(sizeof(unsigned)) +
+                       2 * al(sizeof(unsigned) * (size_t)n * slots_per_image());
+    cudaError_t e = cudaMalloc(&b->arena, planes + b->stats_bytes + kp_bytes + ctl);
+    if (e != cudaSuccess) {
+        delete b;
+        return e == cudaErrorMemoryAllocation ? KAZE_ERR_OOM : KAZE_ERR_CUDA;
+    }
+    char* a = (char*)b->arena;
+    if (cudaMallocHost(&b->h_desc, sizeof(ImageDesc) * n) != cudaSuccess ||
+        cudaMallocHost(&b->h_count_status, sizeof(unsigned) * (n + 1)) != cudaSuccess) {
+        kaze_batch_destroy(b);
+        return KAZE_ERR_CUDA;
+    }
+    char* stats = a + planes;
+    b->stats_base = stats;
+    char* kps = stats + b->stats_bytes;
+    char* c = kps + kp_bytes;
+    b->d_desc = (ImageDesc*)c;
+    c += al(sizeof(ImageDesc) * n);
+    b->d_count_status = (unsigned*)c;
+    c += al(sizeof(unsigned) * (n + 1));
+    b->d_next = (unsigned*)c;
+    c += al(sizeof(unsigned));
+    b->d_done = (unsigned*)c;
+    c += al(sizeof(unsigned) * (size_t)n * slots_per_image());
+    b->d_need = (unsigned*)c;
+
+    for (int i = 0; i < n; ++i) {
+        ImageDesc& d = b->h_desc[i];
+        std::memset(&d, 0, sizeof(d));
+        d.w = w[i];
+        d.h = h[i];
+        d.pitch = b->pitch[i];
+        d.plane = b->plane[i];
+        d.levels = (float*)a;
+        d.doh = d.levels + (size_t)N * d.plane;
+        d.g = d.doh + (size_t)N * d.plane;
+        d.ux = d.g + d.plane;
+        a += al(sizeof(float) * (size_t)d.plane * (2 * N + 2));
+        d.k = (float*)(stats + stat_per * i);
+        d.hmax = (unsigned*)(stats + stat_per * i + al(sizeof(float)));
+        d.hist = (unsigned*)(stats + stat_per * i + al(sizeof(float)) + al(sizeof(unsigned)));
+        d.kp = (kaze_keypoint*)(kps + al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints) * i);
+        d.kp_count = b->d_count_status + i;
+        d.kp_cap = o.max_keypoints;
+        d.mrow = odd_chunk(w[i], 64);
+        d.mcol = odd_chunk(h[i], 64);
+        d.mcol32 = odd_chunk(h[i], 32);
+        d.tiles32_x = (w[i] + 31) / 32;
+        d.tiles64_x = (w[i] + 63) / 64;
+    }
+    P.imgs = b->d_desc;
+    P.next = b->d_next;
+    P.done = b->d_done;
+    P.need = b->d_need;
+    P.status = (int*)(b->d_count_status + n);
+    const kaze_status s = prepare(b);
+    if (s != KAZE_OK) {
+        kaze_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_batch_detect(kaze_batch* b, const float* const* d_imgs, const int* pitches,
+                                       kaze_keypoint* h_out, int capacity_per_image, int* counts)
+{
+    if (!b || capacity_per_image < 0 || (capacity_per_image > 0 && !h_out) || !counts)
+        return bfail(b, KAZE_ERR_INVALID_ARG, "bad output arguments");
+    kaze_status s = set_inputs(b, d_imgs, pitches);
+    if (s != KAZE_OK) return s;
+    s = run(b);
+    if (s != KAZE_OK) return s;
+    KB_TRY(b, cudaStreamSynchronize(b->stream));
+    if (b->h_count_status[b->n]) return bfail(b, KAZE_ERR_TIMEOUT, "a bounded wait of the batched kernel ran out");
+    kaze_status result = KAZE_OK;
+    const unsigned cap = (unsigned)capacity_per_image;
+    for (int i = 0; i < b->n; ++i) {
+        const unsigned total = b->h_count_status[i];
+        const unsigned have = std::min(total, (unsigned)b->opt.max_keypoints);
+        b->hkp.resize(have);
+        if (have) {
+            KB_TRY(b, cudaMemcpyAsync(b->hkp.data(), b->h_desc[i].kp, sizeof(kaze_keypoint) * have,
+                                      cudaMemcpyDeviceToHost, b->stream));
+            KB_TRY(b, cudaStreamSynchronize(b->stream));
+        }
+        std::sort(b->hkp.begin(), b->hkp.end(), [](const kaze_keypoint& x, const kaze_keypoint& y) {
+            if (x.level != y.level) return x.level < y.level;
+            if (x.iy != y.iy) return x.iy < y.iy;
+            return x.ix < y.ix;
+        });
+        const unsigned nout = std::min(have, cap);
+        if (nout) std::memcpy(h_out + (size_t)i * cap, b->hkp.data(), sizeof(kaze_keypoint) * nout);
+        counts[i] = (int)total;
+        if (total > cap || total > (unsigned)b->opt.max_keypoints) result = KAZE_ERR_CAPACITY;
+    }
+    if (result != KAZE_OK) return bfail(b, result, "more keypoints than the output capacity");
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_batch_get_level(kaze_batch* b, int image, int level, const float** d_level, int* pitch)
+{
+    if (!b || image < 0 || image >= b->n || level < 0 || level >= b->N) return KAZE_ERR_INVALID_ARG;
+    if (d_level) *d_level = b->h_desc[image].levels + (size_t)level * b->plane[image];
+    if (pitch) *pitch = b->pitch[image];
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_batch_get_response(kaze_batch* b, int image, int level, const float** d_doh, int* pitch)
+{
+    if (!b || image < 0 || image >= b->n || level < 0 || level >= b->N) return KAZE_ERR_INVALID_ARG;
+    if (d_doh) *d_doh = b->h_desc[image].doh + (size_t)level * b->plane[image];
+    if (pitch) *pitch = b->pitch[image];
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_batch_set_tuning(kaze_batch* b, const kaze_batch_tuning* t)
+{
+    if (!b || !t) return KAZE_ERR_INVALID_ARG;
+    if ((t->cols_per_strip != 4 && t->cols_per_strip != 8) || t->ctas_per_sm < 1 || t->ctas_per_sm > 8)
+        return bfail(b, KAZE_ERR_INVALID_ARG, "tuning out of range");
+    const kaze_batch_tuning old = b->tuning;
+    b->tuning = *t;
+    const kaze_status s = prepare(b);
+    if (s != KAZE_OK) {
+        b->tuning = old;
+        prepare(b);
+    }
+    return s;
+}
+
+KAZE_API kaze_status kaze_batch_get_tuning(const kaze_batch* b, kaze_batch_tuning* t)
+{
+    if (!b || !t) return KAZE_ERR_INVALID_ARG;
+    *t = b->tuning;
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_batch_autotune(kaze_batch* b, const float* const* d_imgs, const int* pitches, int reps,
+                                         kaze_batch_tuning* best, double* best_ms)
+{
+    if (!b || reps < 1) return KAZE_ERR_INVALID_ARG;
+    kaze_status s = set_inputs(b, d_imgs, pitches);
+    if (s != KAZE_OK) return s;
+    const kaze_batch_tuning start = b->tuning;
+    kaze_batch_tuning winner = start;
+    double winner_ms = 1e30;
+    cudaEvent_t e0, e1;
+    KB_TRY(b, cudaEventCreate(&e0));
+    KB_TRY(b, cudaEventCreate(&e1));
+    const int cols_opts[2] = {4, 8};
+    const int cta_opts[2] = {1, 2};
+    for (int ci = 0; ci < 2; ++ci)
+        for (int ti = 0; ti < 2; ++ti) {
+            kaze_batch_tuning cand{cols_opts[ci], cta_opts[ti]};
+            b->tuning = cand;
+            if (prepare(b) != KAZE_OK) {
+                b->err.clear();
+                continue;
+            }
+            if (run(b) != KAZE_OK || cudaStreamSynchronize(b->stream) != cudaSuccess || b->h_count_status[b->n]) {
+                b->err.clear();
+                continue;
+            }
+            float total = 0.f;
+            bool ok = true;
+            for (int r = 0; r < reps && ok; ++r) {
+                ok = cudaEventRecord(e0, b->stream) == cudaSuccess && run(b) == KAZE_OK &&
+                     cudaEventRecord(e1, b->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+                float ms = 0.f;
+                ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && !b->h_count_status[b->n];
+                total += ms;
+            }
+            if (ok && total / reps < winner_ms) {
+                winner_ms = total / reps;
+                winner = cand;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tuning = winner;
+    s = prepare(b);
+    if (s != KAZE_OK) return s;
+    if (winner_ms >= 1e30) return bfail(b, KAZE_ERR_CUDA, "no tuning candidate ran");
+    if (best) *best = winner;
+    if (best_ms) *best_ms = winner_ms;
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_batch_set_wait_limit(kaze_batch* b, long long cycles, int stall_image)
+{
+    if (!b || cycles < 1000) return KAZE_ERR_INVALID_ARG;
+    b->spin_limit = cycles;
+    b->stall_image = stall_image;
+    return prepare(b);
+}
+
+KAZE_API const char* kaze_batch_last_error(const kaze_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+KAZE_API void kaze_batch_destroy(kaze_batch* b)
+{
+    if (!b) return;
+    drop_graph(b);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->arena) cudaFree(b->arena);
+    if (b->h_desc) cudaFreeHost(b->h_desc);
+    if (b->h_count_status) cudaFreeHost(b->h_count_status);
+    delete b;
+}

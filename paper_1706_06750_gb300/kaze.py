@@ -60,6 +60,10 @@ class Keypoint(ctypes.Structure):
     ]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("cols_per_strip", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
 KEYPOINT_DTYPE = np.dtype([
     ("x", np.float32), ("y", np.float32), ("sigma", np.float32), ("response", np.float32),
     ("angle", np.float32), ("level", np.int32), ("octave", np.int32), ("sublevel", np.int32),
@@ -93,6 +97,19 @@ _SIGNATURES = {
     "kaze_op_extrema": (_i, [_vp, _vp, _i, ctypes.c_longlong, _i, _i, _i, ctypes.POINTER(_f),
                              ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
     "kaze_aos_step_static": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _vp]),
+    "kaze_batch_create": (_i, [ctypes.POINTER(Options), _i, ctypes.POINTER(_i), ctypes.POINTER(_i), _vp,
+                               ctypes.POINTER(_vp)]),
+    "kaze_batch_detect": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(Keypoint), _i,
+                               ctypes.POINTER(_i)]),
+    "kaze_batch_get_level": (_i, [_vp, _i, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
+    "kaze_batch_get_response": (_i, [_vp, _i, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
+    "kaze_batch_get_tuning": (_i, [_vp, ctypes.POINTER(BatchTuning)]),
+    "kaze_batch_set_tuning": (_i, [_vp, ctypes.POINTER(BatchTuning)]),
+    "kaze_batch_autotune": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), _i, ctypes.POINTER(BatchTuning),
+                                 ctypes.POINTER(ctypes.c_double)]),
+    "kaze_batch_set_wait_limit": (_i, [_vp, ctypes.c_longlong, _i]),
+    "kaze_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "kaze_batch_destroy": (None, [_vp]),
     "kaze_kernel_kinds": (_i, []),
     "kaze_kernel_name": (ctypes.c_char_p, [_i]),
     "kaze_last_launch_count": (_i, [_vp]),
@@ -421,3 +438,163 @@ class Kaze:
         self.last_status = st
         self.last_count = cnt.value
         return _sorted_keypoints(buf, min(cnt.value, cap))
+
+
+class Batch:
+    """A batch handle (kaze_batch): the whole detection of a fixed list of
+    images of mixed sizes in one persistent launch."""
+
+    def __init__(self, sizes, options: Options | None = None, stream=None, **overrides):
+        import torch
+        self._L = lib()
+        opt = options if options is not None else default_options()
+        for k, v in overrides.items():
+            setattr(opt, k, v)
+        self.options = opt
+        self.sizes = [(int(w), int(h)) for w, h in sizes]
+        self.n = len(self.sizes)
+        self.n_levels = opt.octaves * opt.sublevels
+        self._stream = stream if stream is not None else torch.cuda.Stream()
+        ws = (_i * self.n)(*[w for w, _ in self.sizes])
+        hs = (_i * self.n)(*[h for _, h in self.sizes])
+        h = _vp()
+        st = self._L.kaze_batch_create(ctypes.byref(opt), self.n, ws, hs, _vp(self._stream.cuda_stream),
+                                       ctypes.byref(h))
+        if st != OK:
+            raise KazeError(st, f"kaze_batch_create failed: {self._L.kaze_status_string(st).decode()}")
+        self._h = h
+        self._cap = opt.max_keypoints
+        self._kp_buf = None
+
+    def _ck(self, st, what):
+        if st != OK and st != ERR_CAPACITY:
+            msg = self._L.kaze_batch_last_error(self._h).decode()
+            raise KazeError(st, f"{what}: {self._L.kaze_status_string(st).decode()}: {msg}")
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.kaze_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def _inputs(self, imgs):
+        if len(imgs) != self.n:
+            raise KazeError(ERR_INVALID_ARG, f"expected {self.n} images")
+        ptrs = (_vp * self.n)()
+        pitches = (_i * self.n)()
+        for i, t in enumerate(imgs):
+            w, h, pitch = _check_image(t)
+            if (w, h) != self.sizes[i]:
+                raise KazeError(ERR_INVALID_ARG, f"image {i} is {w}x{h}, expected {self.sizes[i]}")
+            ptrs[i] = t.data_ptr()
+            pitches[i] = pitch
+        return ptrs, pitches
+
+    def _begin(self):
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur != self._stream:
+            self._stream.wait_stream(cur)
+
+    def detect(self, imgs, capacity=None):
+        """Keypoints of every image: a list of KEYPOINT_DTYPE arrays."""
+        cap = self._cap if capacity is None else int(capacity)
+        ptrs, pitches = self._inputs(imgs)
+        if self._kp_buf is None or len(self._kp_buf) < cap * self.n:
+            self._kp_buf = (Keypoint * (cap * self.n))()
+        counts = (_i * self.n)()
+        self._begin()
+        st = self._ck(self._L.kaze_batch_detect(self._h, ptrs, pitches, self._kp_buf, cap, counts),
+                      "kaze_batch_detect")
+        self.last_status = st
+        self.last_counts = list(counts)
+        raw = np.frombuffer(self._kp_buf, dtype=KEYPOINT_DTYPE, count=cap * self.n)
+        return [raw[i * cap: i * cap + min(counts[i], cap)].copy() for i in range(self.n)]
+
+    def level(self, image, level):
+        import torch
+        p = _vp()
+        pitch = _i()
+        self._ck(self._L.kaze_batch_get_level(self._h, int(image), int(level), ctypes.byref(p),
+                                              ctypes.byref(pitch)), "kaze_batch_get_level")
+        w, h = self.sizes[image]
+        return torch.as_tensor(_DeviceView(p.value, h, w, pitch.value), device="cuda").clone()
+
+    def response(self, image, level):
+        import torch
+        p = _vp()
+        pitch = _i()
+        self._ck(self._L.kaze_batch_get_response(self._h, int(image), int(level), ctypes.byref(p),
+                                                 ctypes.byref(pitch)), "kaze_batch_get_response")
+        w, h = self.sizes[image]
+        return torch.as_tensor(_DeviceView(p.value, h, w, pitch.value), device="cuda").clone()
+
+    def tuning(self):
+        t = BatchTuning()
+        self._ck(self._L.kaze_batch_get_tuning(self._h, ctypes.byref(t)), "kaze_batch_get_tuning")
+        return (t.cols_per_strip, t.ctas_per_sm)
+
+    def set_tuning(self, cols_per_strip, ctas_per_sm):
+        t = BatchTuning(int(cols_per_strip), int(ctas_per_sm))
+        self._ck(self._L.kaze_batch_set_tuning(self._h, ctypes.byref(t)), "kaze_batch_set_tuning")
+
+    def autotune(self, imgs, reps=3, cache=None):
+        """Times every solve-tile shape on these images and keeps the fastest.
+
+        With `cache` (a JSON path) the choice is stored under a key made of
+        the device name and the size list, and reused when present."""
+        import json
+        import os
+        import torch
+        key = None
+        if cache:
+            key = torch.cuda.get_device_name() + "|" + ",".join(f"{w}x{h}" for w, h in sorted(self.sizes))
+            try:
+                with open(cache) as f:
+                    known = json.load(f)
+                if key in known:
+                    self.set_tuning(*known[key]["tuning"])
+                    return tuple(known[key]["tuning"]), known[key]["ms"]
+            except (OSError, ValueError, KeyError):
+                pass
+        ptrs, pitches = self._inputs(imgs)
+        best = BatchTuning()
+        ms = ctypes.c_double()
+        self._begin()
+        self._ck(self._L.kaze_batch_autotune(self._h, ptrs, pitches, int(reps), ctypes.byref(best),
+                                             ctypes.byref(ms)), "kaze_batch_autotune")
+        result = (best.cols_per_strip, best.ctas_per_sm)
+        if cache:
+            try:
+                with open(cache) as f:
+                    known = json.load(f)
+            except (OSError, ValueError):
+                known = {}
+            known[key] = {"tuning": list(result), "ms": ms.value}
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            with open(cache, "w") as f:
+                json.dump(known, f, indent=1)
+        return result, ms.value
+
+    def set_wait_limit(self, cycles, stall_image=-1):
+        """Test hook: bound of a device-side wait in SM cycles; stall_image
+        >= 0 makes one stage of that image wait for an item that never
+        exists, so the next detect reports ERR_TIMEOUT."""
+        self._ck(self._L.kaze_batch_set_wait_limit(self._h, int(cycles), int(stall_image)),
+                 "kaze_batch_set_wait_limit")

@@ -1,0 +1,122 @@
+"""The batched persistent path (kaze_batch_*) against the single-image path
+and the oracle, its solve-tile shapes and its bounded waits (needs a GPU)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1706_06750_gb300 import synth  # noqa: E402
+
+from kp_match import compare  # noqa: E402
+
+SIZES = [(160, 120), (257, 131), (96, 96), (64, 200), (300, 40), (130, 130)]
+
+
+@pytest.fixture(scope="module")
+def kz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_06750_gb300 import build, kaze
+    build.build()
+    oracle.build()
+    return kaze
+
+
+def images(sizes, seed0=500):
+    return [synth.image(w, h, seed0 + j) for j, (w, h) in enumerate(sizes)]
+
+
+def single_path(kz, img, **kw):
+    h, w = img.shape
+    with kz.Kaze(w, h, octaves=2, sublevels=4, **kw) as k:
+        x = torch.from_numpy(img).cuda()
+        k.build_scale_space(x)
+        kval = k.contrast()
+        lv = k.levels().cpu().numpy()
+        k.detector_response()
+        D = k.responses().cpu().numpy()
+        kp = k.find_extrema()
+    return lv, D, kp, kval
+
+
+def test_batch_matches_single_image_path(kz):
+    imgs = images(SIZES)
+    xs = [torch.from_numpy(a).cuda() for a in imgs]
+    with kz.Batch(SIZES, octaves=2, sublevels=4) as b:
+        kps = b.detect(xs)
+        for i, img in enumerate(imgs):
+            lv, D, kp, _ = single_path(kz, img)
+            for l in range(8):
+                assert np.max(np.abs(b.level(i, l).cpu().numpy() - lv[l])) <= 2e-6, (i, l)
+                dm = np.max(np.abs(D[l]))
+                assert np.max(np.abs(b.response(i, l).cpu().numpy() - D[l])) <= 1e-5 * dm + 1e-12, (i, l)
+            ov = compare(kp, kps[i], D.astype(np.float64))[0]
+            assert ov >= 0.995, (i, len(kp), len(kps[i]))
+
+
+@pytest.mark.parametrize("tuning", [(4, 1), (4, 2), (8, 1), (8, 2)])
+def test_every_tile_shape_gives_the_same_result(kz, tuning):
+    imgs = images(SIZES[:3], 700)
+    xs = [torch.from_numpy(a).cuda() for a in imgs]
+    with kz.Batch(SIZES[:3], octaves=2, sublevels=4) as b:
+        ref = b.detect(xs)
+        L7 = [b.level(i, 7).cpu().numpy() for i in range(3)]
+        b.set_tuning(*tuning)
+        assert b.tuning()[0] == tuning[0]
+        got = b.detect(xs)
+        for i in range(3):
+            assert np.max(np.abs(b.level(i, 7).cpu().numpy() - L7[i])) <= 2e-6
+            assert len(got[i]) == len(ref[i])
+
+
+def test_batch_against_oracle(kz):
+    img = synth.image(200, 150, 901)
+    L0 = oracle.gaussian(img.astype(np.float64), 1.6)
+    kf = float(np.float32(oracle.contrast_k(L0)[0]))
+    x = torch.from_numpy(img).cuda()
+    with kz.Batch([(200, 150), (96, 64)], octaves=2, sublevels=4, k_override=kf) as b:
+        kps = b.detect([x, torch.rand(64, 96, device="cuda")])
+        lv = np.stack([b.level(0, l).cpu().numpy() for l in range(8)]).astype(np.float64)
+        D = np.stack([b.response(0, l).cpu().numpy() for l in range(8)]).astype(np.float64)
+    opt = oracle.Options.make(octaves=2, sublevels=4, k_override=kf, dthreshold=float(np.float32(0.001)))
+    lv_r, D_r, kp_r, _ = oracle.kaze_detect(img.astype(np.float64), opt)
+    assert np.max(np.abs(lv - lv_r)) <= 2e-5
+    dmax = np.max(np.abs(D_r), axis=(1, 2))
+    assert np.all(np.max(np.abs(D - D_r), axis=(1, 2)) <= 1e-4 * dmax + 1e-12)
+    assert compare(kp_r, kps[0], D_r)[0] >= 0.995
+
+
+def test_stalled_dependency_times_out_and_the_handle_recovers(kz):
+    imgs = images(SIZES[:3], 800)
+    xs = [torch.from_numpy(a).cuda() for a in imgs]
+    with kz.Batch(SIZES[:3], octaves=2, sublevels=4) as b:
+        ref = b.detect(xs)
+        b.set_wait_limit(1 << 24, stall_image=1)  # ~10 ms per wait
+        with pytest.raises(kz.KazeError) as e:
+            b.detect(xs)
+        assert e.value.status == kz.ERR_TIMEOUT
+        b.set_wait_limit(1 << 31, stall_image=-1)
+        again = b.detect(xs)
+        for i in range(3):
+            assert np.array_equal(again[i], ref[i])
+
+
+def test_mixed_size_workload_sample(kz):
+    """The 64-image mixed-size workload: three images checked against the
+    single-image path, keypoint counts sane for all."""
+    sizes = synth.batch_sizes(64)
+    imgs = synth.batch_images(64)
+    xs = [torch.from_numpy(a).cuda() for a in imgs]
+    with kz.Batch(sizes) as b:
+        kps = b.detect(xs)
+    assert all(len(k) > 10 for k in kps)
+    for i in (0, 17, 63):
+        h, w = imgs[i].shape
+        with kz.Kaze(w, h) as k:
+            ref = k.detect(xs[i])
+        got = {(int(r["level"]), int(r["iy"]), int(r["ix"])) for r in kps[i]}
+        want = {(int(r["level"]), int(r["iy"]), int(r["ix"])) for r in ref}
+        assert len(got & want) >= 0.995 * max(len(got), len(want)), (i, len(got), len(want))
