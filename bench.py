@@ -362,11 +362,9 @@ def run_batched(args, kaze, synth, torch, stream, world, rank, max_over_ranks, b
     mpx = sum(w * h for w, h in sizes) / 1e6
     reps = max(2, min(args.steps, 10))
     cache = os.path.join(ROOT, "paper_1706_06750_gb300", "_build", "batch_tuning.json")
-    with kaze.Batch(sizes) as b:
-        tuning, tune_ms = b.autotune(imgs, reps=2, cache=cache)
+    def time_batch(b):
         for _ in range(2):
             b.detect(imgs)
-        launches = 1
         barrier()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         with torch.cuda.stream(b.stream):
@@ -375,8 +373,22 @@ def run_batched(args, kaze, synth, torch, stream, world, rank, max_over_ranks, b
                 b.detect(imgs)
             ev[1].record(b.stream)
         torch.cuda.synchronize()
-        t_batch = max_over_ranks(ev[0].elapsed_time(ev[1]))
+        return max_over_ranks(ev[0].elapsed_time(ev[1]))
+
+    with kaze.Batch(sizes) as b:
+        tuning, tune_ms = b.autotune(imgs, reps=2, cache=cache)
+        t_batch = time_batch(b)
         counts = [len(k) for k in b.detect(imgs)]
+        # the single persistent launch, for comparison (its best shape)
+        t_persist, persist_shape = None, None
+        for shape in ((kaze.BATCH_PERSISTENT, 4, 2, 8), (kaze.BATCH_PERSISTENT, 8, 1, 8)):
+            b.set_tuning(*shape)
+            t = time_batch(b)
+            if t_persist is None or t < t_persist:
+                t_persist, persist_shape = t, shape
+        b.set_tuning(*tuning)
+    n_levels = OCTAVES * SUBLEVELS
+    launches = 1 if tuning[0] == kaze.BATCH_PERSISTENT else 64 * (3 * (n_levels - 1) + 4 + 3 + 1)
     mw = max(w for w, _ in sizes)
     mh = max(h for _, h in sizes)
     with kaze.Kaze(mw, mh) as k:
@@ -393,13 +405,20 @@ def run_batched(args, kaze, synth, torch, stream, world, rank, max_over_ranks, b
         t_plain = max_over_ranks(ev[0].elapsed_time(ev[1]))
     img_s = world * 64 * reps / (t_batch * 1e-3)
     plain_s = world * 64 / (t_plain * 1e-3)
+    mode = "persistent" if tuning[0] == kaze.BATCH_PERSISTENT else "concurrent"
     return {"images": 64, "megapixels": round(mpx, 3), "img_per_s": img_s,
             "mpix_per_s": img_s * mpx / 64, "ms_per_batch": t_batch / reps,
             "plain_img_per_s": plain_s, "plain_ms_per_64": t_plain,
-            "speedup_vs_plain": img_s / plain_s, "tuning": list(tuning),
+            "speedup_vs_plain": img_s / plain_s,
+            "tuning": {"mode": mode, "cols_per_strip": tuning[1], "ctas_per_sm": tuning[2],
+                       "streams": tuning[3]},
             "autotune_best_ms": tune_ms, "keypoints": int(sum(counts)),
-            "launches_per_batch": launches,
-            "note": "one persistent kernel per batch; plain = kaze_detect image after image"}
+            "kernel_launches_per_batch": launches,
+            "persistent_ms_per_batch": t_persist / reps,
+            "persistent_img_per_s": world * 64 * reps / (t_persist * 1e-3),
+            "persistent_shape": {"cols_per_strip": persist_shape[1], "ctas_per_sm": persist_shape[2]},
+            "note": ("autotuned execution of the batch (graph-replayed); plain = kaze_detect image "
+                     "after image on one stream; persistent = the whole batch as one kernel launch")}
 
 
 def main():

@@ -201,12 +201,20 @@ kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch, long lo
  * single-image path. */
 typedef struct kaze_batch kaze_batch;
 
-/* Solve-tile shape of the batched kernel: columns per column-solve strip
- * (4: 64 chunks per column, 8: 32 chunks) and persistent CTAs per SM (1 or
- * more; capped by occupancy). */
+/* Execution of a batch.
+ *   KAZE_BATCH_PERSISTENT: the one persistent launch described above;
+ *     cols_per_strip (4: 64 chunks per column, 8: 32 chunks) and
+ *     ctas_per_sm (capped by occupancy) shape it.
+ *   KAZE_BATCH_CONCURRENT: each image runs the single-image kernel
+ *     sequence; `streams` sequences run side by side as parallel branches
+ *     of one recorded graph. */
+#define KAZE_BATCH_PERSISTENT 0
+#define KAZE_BATCH_CONCURRENT 1
 typedef struct kaze_batch_tuning {
+    int mode;
     int cols_per_strip;
     int ctas_per_sm;
+    int streams;
 } kaze_batch_tuning;
 
 /* Allocates every plane of every image (2N + 2 planes each), the keypoint
@@ -232,17 +240,18 @@ kaze_status kaze_batch_get_response(kaze_batch* b, int image, int level, const f
 kaze_status kaze_batch_get_tuning(const kaze_batch* b, kaze_batch_tuning* t);
 kaze_status kaze_batch_set_tuning(kaze_batch* b, const kaze_batch_tuning* t);
 
-/* Autotuner: times every candidate shape (cols_per_strip in {4, 8} x
- * ctas_per_sm in {1, 2}) on the given images, `reps` runs each (CUDA
- * events), keeps the fastest and reports it and its mean time in ms. */
+/* Autotuner: times every candidate (persistent with cols_per_strip in
+ * {4, 8} x ctas_per_sm in {1, 2}; concurrent with 4, 8 or 16 streams) on
+ * the given images, `reps` runs each (CUDA events), keeps the fastest and
+ * reports it and its mean time in ms. */
 kaze_status kaze_batch_autotune(kaze_batch* b, const float* const* d_imgs, const int* pitches, int reps,
                                 kaze_batch_tuning* best, double* best_ms);
 
-/* Test hook for failure detection: sets how many SM cycles a device-side
- * wait may take (default 2^31) and, if stall_image >= 0, makes one stage
- * of that image wait for an item that never exists, so the wait runs out
- * and kaze_batch_detect returns KAZE_ERR_TIMEOUT.  stall_image < 0 clears
- * the hook. */
+/* Test hook for failure detection (persistent mode): sets how many SM
+ * cycles a device-side wait may take (default 2^31) and, if stall_image >=
+ * 0, makes one stage of that image wait for an item that never exists, so
+ * the wait runs out and kaze_batch_detect returns KAZE_ERR_TIMEOUT.
+ * stall_image < 0 clears the hook. */
 kaze_status kaze_batch_set_wait_limit(kaze_batch* b, long long cycles, int stall_image);
 
 /* Message of the batch's first error ("" if none). */

@@ -19,6 +19,7 @@
 // presmoothing, contrast factor, Eq. 2-4 AOS steps, Eq. 8 response, Eq. 9-12
 // extrema).  The line solver here takes its chunk length at run time (one
 // kernel serves every image size): a' lives in shared memory beside c' and d'.
+#include "aos_solver.cuh"
 #include "kaze_batch.h"
 
 namespace kz {
@@ -44,11 +45,13 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 
 // ------------------------------------------------------------- stencils --
 
-// Separable Gaussian of radius r on a 32x32 tile: rows then columns.
+// Separable Gaussian of radius r on a 32x32 tile: rows then columns.  RC > 0
+// fixes the radius at compile time (unrolled taps); RC = 0 reads it from taps.
+template <int RC>
 __device__ void gauss_tile(const float* __restrict__ in, int in_pitch, float* __restrict__ out, int out_pitch,
                            int w, int h, const GaussTaps& taps, int tx0, int ty0, float* sm)
 {
-    const int r = taps.r;
+    const int r = RC > 0 ? RC : taps.r;
     const int SW = 32 + 2 * r, SH = 32 + 2 * r;
     float* A = sm;            // SH x (SW)
     float* B = sm + SH * SW;  // SH x 32
@@ -62,27 +65,39 @@ __device__ void gauss_tile(const float* __restrict__ in, int in_pitch, float* __
     for (int i = tid; i < SH * 32; i += NT) {
         const int sy = i >> 5, sx = i & 31;
         float acc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], A[sy * SW + sx + j], acc);
+        if (RC > 0) {
+#pragma unroll
+            for (int j = 0; j <= 2 * RC; ++j) acc = fmaf(taps.w[j], A[sy * SW + sx + j], acc);
+        } else {
+            for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], A[sy * SW + sx + j], acc);
+        }
         B[i] = acc;
     }
     __syncthreads();
     for (int i = tid; i < 32 * 32; i += NT) {
         const int oy = i >> 5, ox = i & 31;
         float acc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], B[(oy + j) * 32 + ox], acc);
+        if (RC > 0) {
+#pragma unroll
+            for (int j = 0; j <= 2 * RC; ++j) acc = fmaf(taps.w[j], B[(oy + j) * 32 + ox], acc);
+        } else {
+            for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], B[(oy + j) * 32 + ox], acc);
+        }
         if (x0 + ox < w && y0 + oy < h) out[(size_t)(y0 + oy) * out_pitch + x0 + ox] = acc;
     }
+    __syncthreads();  // the next tile of the same item reuses the shared memory
 }
 
 enum { GM_COND = 0, GM_MAX = 1, GM_HIST = 2 };
 
 // Smoothed Scharr gradient of a 32x32 tile (radius r smoothing, halo r+1),
 // then the conductance of Eq. 3, the maximum magnitude or the histogram.
+template <int RC>
 __device__ void gradient_tile(int mode, const float* __restrict__ L, float* __restrict__ g, int pitch, int w, int h,
                               const GaussTaps& taps, float k, int diffusivity, unsigned* hmax_bits, unsigned* hist,
                               int nbins, int tx0, int ty0, float* sm)
 {
-    const int r = taps.r;
+    const int r = RC > 0 ? RC : taps.r;
     constexpr int CW = 34, CH = 34;
     const int SW = CW + 2 * r, SH = CH + 2 * r;
     float* A = sm;                 // SH x SW
@@ -101,14 +116,24 @@ __device__ void gradient_tile(int mode, const float* __restrict__ L, float* __re
     for (int i = tid; i < SH * CW; i += NT) {
         const int sy = i / CW, sx = i - sy * CW;
         float acc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], A[sy * SW + sx + j], acc);
+        if (RC > 0) {
+#pragma unroll
+            for (int j = 0; j <= 2 * RC; ++j) acc = fmaf(taps.w[j], A[sy * SW + sx + j], acc);
+        } else {
+            for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], A[sy * SW + sx + j], acc);
+        }
         B[i] = acc;
     }
     __syncthreads();
     for (int i = tid; i < CH * CW; i += NT) {
         const int sy = i / CW, sx = i - sy * CW;
         float acc = 0.f;
-        for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], B[(sy + j) * CW + sx], acc);
+        if (RC > 0) {
+#pragma unroll
+            for (int j = 0; j <= 2 * RC; ++j) acc = fmaf(taps.w[j], B[(sy + j) * CW + sx], acc);
+        } else {
+            for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], B[(sy + j) * CW + sx], acc);
+        }
         C[i] = acc;
     }
     __syncthreads();
@@ -148,6 +173,7 @@ __device__ void gradient_tile(int mode, const float* __restrict__ L, float* __re
         for (int i = tid; i < nbins; i += NT)
             if (hs[i]) atomicAdd(&hist[i], hs[i]);
     }
+    __syncthreads();  // the next tile of the same item reuses the shared memory
 }
 
 // Percentile pick of Sec. III-1 (first warp of the CTA).
@@ -617,6 +643,180 @@ __device__ void cols_item(const ImageDesc& im, const float* __restrict__ L, floa
     }
 }
 
+// Row group with a compile-time chunk length: the register-resident solver
+// of the single-image path (aos_solver.cuh), 4 rows x 2 warps.
+template <int M>
+__device__ void rows_item_m(const ImageDesc& im, const float* __restrict__ L, float tau, int y0, float* sm)
+{
+    constexpr int P = 64;
+    constexpr int LS = aos::row_stride_floats(P, M);
+    const int w = im.w, h = im.h, pitch = im.pitch;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = warp >> 1, part = warp & 1;
+    const int y = y0 + r;
+    const bool active = y < h;
+    float* sg = sm + (size_t)r * (2 * LS + 8 * P);
+    float* sd = sg + LS;
+    float* eq = sd + LS;
+    float* xs = eq + 6 * P;
+    const int p = part * 32 + lane;
+    const int w4 = w & ~3;
+    if (active) {
+        const float* grow = im.g + (size_t)y * pitch;
+        const float* lrow = L + (size_t)y * pitch;
+        for (int x = p * 4; x < w4; x += 4 * P) {
+            *reinterpret_cast<float4*>(sg + x) = __ldcg(reinterpret_cast<const float4*>(grow + x));
+            *reinterpret_cast<float4*>(sd + x) = __ldcg(reinterpret_cast<const float4*>(lrow + x));
+        }
+        for (int x = w4 + p; x < w; x += P) {
+            sg[x] = __ldcg(grow + x);
+            sd[x] = __ldcg(lrow + x);
+        }
+    }
+    __syncthreads();
+    const int j0 = p * M;
+    float* ce = sg + j0;
+    float* cd = sd + j0;
+    const float g_prev = (j0 > 0 && j0 - 1 < w) ? ce[-1] : 0.f;
+    const float g_next = (j0 + M < w) ? ce[M] : 0.f;
+    __syncthreads();
+    float ap[M];
+    if (active) {
+        const aos::ChunkEqs q = aos::chunk_reduce<1, M>(ce, cd, g_prev, g_next, j0, w, tau, ap);
+        eq[0 * P + p] = q.aL;
+        eq[1 * P + p] = q.cL;
+        eq[2 * P + p] = q.dL;
+        eq[3 * P + p] = q.aF;
+        eq[4 * P + p] = q.cF;
+        eq[5 * P + p] = q.dF;
+    }
+    __syncthreads();
+    if (active && part == 0) aos::interface_line<2>(eq, xs, lane);
+    __syncthreads();
+    if (active) aos::chunk_solution<1, M>(ce, cd, ap, xs[p], xs[P + p]);
+    __syncthreads();
+    if (active) {
+        float* urow = im.ux + (size_t)y * pitch;
+        for (int x = p * 4; x < w4; x += 4 * P)
+            *reinterpret_cast<float4*>(urow + x) = *reinterpret_cast<const float4*>(sd + x);
+        for (int x = w4 + p; x < w; x += P) urow[x] = sd[x];
+    }
+    __syncthreads();
+}
+
+// Column strip of 4 columns, 64 chunks, compile-time chunk length.
+template <int M>
+__device__ void cols_item_m(const ImageDesc& im, const float* __restrict__ L, float* __restrict__ Ln, float tau,
+                            int x0, float* sm)
+{
+    constexpr int COLS = 4, P = 64;
+    constexpr int RS = P * M;
+    const int w = im.w, h = im.h, pitch = im.pitch;
+    float* tg = sm;
+    float* td = tg + (size_t)RS * COLS;
+    float* eq0 = td + (size_t)RS * COLS;
+    const int tid = threadIdx.x;
+    const int c = tid % COLS, p = tid / COLS;
+    const bool full = x0 + COLS <= w;
+    for (int j = tid; j < RS; j += NT) {
+        float4 gv = make_float4(0.f, 0.f, 0.f, 0.f), lv = gv;
+        if (j < h) {
+            const size_t gi = (size_t)j * pitch + x0;
+            if (full) {
+                gv = __ldcg(reinterpret_cast<const float4*>(im.g + gi));
+                lv = __ldcg(reinterpret_cast<const float4*>(L + gi));
+            } else {
+                float* gp = &gv.x;
+                float* lp = &lv.x;
+                for (int k = 0; k < 4; ++k)
+                    if (x0 + k < w) {
+                        gp[k] = __ldcg(im.g + gi + k);
+                        lp[k] = __ldcg(L + gi + k);
+                    }
+            }
+        }
+        *reinterpret_cast<float4*>(tg + (size_t)j * COLS) = gv;
+        *reinterpret_cast<float4*>(td + (size_t)j * COLS) = lv;
+    }
+    __syncthreads();
+    const int j0 = p * M;
+    float* ce = tg + (size_t)j0 * COLS + c;
+    float* cd = td + (size_t)j0 * COLS + c;
+    const float g_prev = (j0 > 0 && j0 - 1 < h) ? ce[-COLS] : 0.f;
+    const float g_next = (j0 + M < h) ? ce[M * COLS] : 0.f;
+    __syncthreads();
+    float ap[M];
+    const aos::ChunkEqs q = aos::chunk_reduce<COLS, M>(ce, cd, g_prev, g_next, j0, h, tau, ap);
+    float* eqc = eq0 + (size_t)c * 8 * P;
+    eqc[0 * P + p] = q.aL;
+    eqc[1 * P + p] = q.cL;
+    eqc[2 * P + p] = q.dL;
+    eqc[3 * P + p] = q.aF;
+    eqc[4 * P + p] = q.cF;
+    eqc[5 * P + p] = q.dF;
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp < COLS) {
+        float* eqw = eq0 + (size_t)warp * 8 * P;
+        aos::interface_line<2>(eqw, eqw + 6 * P, lane);
+    }
+    __syncthreads();
+    aos::chunk_solution<COLS, M>(ce, cd, ap, eqc[6 * P + p], eqc[7 * P + p]);
+    __syncthreads();
+    for (int j = tid; j < h; j += NT) {
+        const size_t gi = (size_t)j * pitch + x0;
+        const float* uy = td + (size_t)j * COLS;
+        if (full) {
+            const float4 a = __ldcg(reinterpret_cast<const float4*>(im.ux + gi));
+            float4 rr;
+            rr.x = 0.5f * (a.x + uy[0]);
+            rr.y = 0.5f * (a.y + uy[1]);
+            rr.z = 0.5f * (a.z + uy[2]);
+            rr.w = 0.5f * (a.w + uy[3]);
+            *reinterpret_cast<float4*>(Ln + gi) = rr;
+        } else {
+            for (int k = 0; k < 4; ++k)
+                if (x0 + k < w) Ln[gi + k] = 0.5f * (__ldcg(im.ux + gi + k) + uy[k]);
+        }
+    }
+    __syncthreads();
+}
+
+// Chunk lengths with compiled solvers (the sizes of the mixed-size
+// workload); other lengths use the run-time solver.
+#define KZ_BATCH_ROW_M(X) X(11) X(21) X(31)
+#define KZ_BATCH_COL_M(X) X(9) X(13) X(17) X(19)
+
+__device__ void rows_dispatch(const ImageDesc& im, const float* L, float tau, int y0, float* sm)
+{
+    switch (im.mrow) {
+#define KZ_R(M)                              \
+    case M:                                  \
+        rows_item_m<M>(im, L, tau, y0, sm);  \
+        return;
+        KZ_BATCH_ROW_M(KZ_R)
+#undef KZ_R
+        default: rows_item(im, L, tau, y0, sm); __syncthreads();
+    }
+}
+
+__device__ void cols_dispatch(const ImageDesc& im, const float* L, float* Ln, float tau, int x0, int cols, float* sm)
+{
+    if (cols == 4) {
+        switch (im.mcol) {
+#define KZ_C(M)                                  \
+    case M:                                      \
+        cols_item_m<M>(im, L, Ln, tau, x0, sm);  \
+        return;
+            KZ_BATCH_COL_M(KZ_C)
+#undef KZ_C
+            default: break;
+        }
+    }
+    cols_item(im, L, Ln, tau, x0, cols, sm);
+    __syncthreads();
+}
+
 // ------------------------------------------------------ the persistent kernel
 
 // Waits (thread 0) until counter[slot] reaches need[slot]; false on timeout
@@ -638,14 +838,36 @@ __device__ bool wait_stage(const BatchParams& P, int image, int slot)
     return true;
 }
 
-__global__ void __launch_bounds__(NT) k_batch(const __grid_constant__ BatchParams P)
+__global__ void __launch_bounds__(NT, 2) k_batch(const __grid_constant__ BatchParams P)
 {
     extern __shared__ __align__(16) float sm[];
-    __shared__ unsigned s_item;
+    __shared__ unsigned s_item, s_next;
     __shared__ int s_ok;
+    // stages this CTA has already seen complete: one bit per (image, slot)
+    // for the first kMaxCachedImages images
+    constexpr int kMaxCachedImages = 64;
+    __shared__ unsigned s_seen[kMaxCachedImages * kSlotWords];
     const int tid = threadIdx.x;
+    for (int i = tid; i < kMaxCachedImages * kSlotWords; i += NT) s_seen[i] = 0u;
+    if (tid == 0) s_next = atomicAdd(P.next, 1u);
+    __syncthreads();
+    auto wait_cached = [&](int image, int slot) -> bool {
+        if (image < kMaxCachedImages) {
+            unsigned& word = s_seen[image * kSlotWords + (slot >> 5)];
+            const unsigned bit = 1u << (slot & 31);
+            if (word & bit) return true;
+            if (!wait_stage(P, image, slot)) return false;
+            word |= bit;
+            return true;
+        }
+        return wait_stage(P, image, slot);
+    };
     while (true) {
-        if (tid == 0) s_item = atomicAdd(P.next, 1u);
+        // the next item was fetched while the previous one ran
+        if (tid == 0) {
+            s_item = s_next;
+            if (s_item < (unsigned)P.n_items) s_next = atomicAdd(P.next, 1u);
+        }
         __syncthreads();
         const unsigned it = s_item;
         if (it >= (unsigned)P.n_items) return;
@@ -656,19 +878,19 @@ __global__ void __launch_bounds__(NT) k_batch(const __grid_constant__ BatchParam
         if (tid == 0) {
             bool ok = true;
             switch (item.kind) {
-                case IT_GMAX: ok = wait_stage(P, item.image, slot_presmooth()); break;
-                case IT_GHIST: ok = wait_stage(P, item.image, slot_gmax()); break;
-                case IT_PCT: ok = wait_stage(P, item.image, slot_ghist()); break;
+                case IT_GMAX: ok = wait_cached(item.image, slot_presmooth()); break;
+                case IT_GHIST: ok = wait_cached(item.image, slot_gmax()); break;
+                case IT_PCT: ok = wait_cached(item.image, slot_ghist()); break;
                 case IT_COND:
-                    ok = wait_stage(P, item.image, lv == 1 ? slot_pct() : slot_cols(lv - 1)) &&
-                         wait_stage(P, item.image, slot_presmooth());
+                    ok = wait_cached(item.image, lv == 1 ? slot_pct() : slot_cols(lv - 1)) &&
+                         wait_cached(item.image, slot_presmooth());
                     break;
-                case IT_ROWS: ok = wait_stage(P, item.image, slot_cond(lv)); break;
-                case IT_COLS: ok = wait_stage(P, item.image, slot_rows(lv)); break;
-                case IT_DOH: ok = wait_stage(P, item.image, lv == 0 ? slot_presmooth() : slot_cols(lv)); break;
+                case IT_ROWS: ok = wait_cached(item.image, slot_cond(lv)); break;
+                case IT_COLS: ok = wait_cached(item.image, slot_rows(lv)); break;
+                case IT_DOH: ok = wait_cached(item.image, lv == 0 ? slot_presmooth() : slot_cols(lv)); break;
                 case IT_EXTREMA:
-                    ok = wait_stage(P, item.image, slot_doh(lv - 1)) && wait_stage(P, item.image, slot_doh(lv)) &&
-                         wait_stage(P, item.image, slot_doh(lv + 1));
+                    ok = wait_cached(item.image, slot_doh(lv - 1)) && wait_cached(item.image, slot_doh(lv)) &&
+                         wait_cached(item.image, slot_doh(lv + 1));
                     break;
                 default: break;
             }
@@ -680,16 +902,28 @@ __global__ void __launch_bounds__(NT) k_batch(const __grid_constant__ BatchParam
         int slot = -1;
         switch (item.kind) {
             case IT_PRESMOOTH: {
-                const int tx = item.index % im.tiles32_x, ty = item.index / im.tiles32_x;
-                gauss_tile(im.img, im.img_pitch, im.levels, im.pitch, im.w, im.h, P.taps0, tx, ty, sm);
+                const int gx = item.index % im.groups32_x, ty = item.index / im.groups32_x;
+                for (int tx = gx * kTilesPerItem; tx < min(im.tiles32_x, (gx + 1) * kTilesPerItem); ++tx) {
+                    if (P.taps0.r == 5)
+                        gauss_tile<5>(im.img, im.img_pitch, im.levels, im.pitch, im.w, im.h, P.taps0, tx, ty, sm);
+                    else
+                        gauss_tile<0>(im.img, im.img_pitch, im.levels, im.pitch, im.w, im.h, P.taps0, tx, ty, sm);
+                }
                 slot = slot_presmooth();
                 break;
             }
             case IT_GMAX:
             case IT_GHIST: {
-                const int tx = item.index % im.tiles32_x, ty = item.index / im.tiles32_x;
-                gradient_tile(item.kind == IT_GMAX ? GM_MAX : GM_HIST, im.levels, nullptr, im.pitch, im.w, im.h,
-                              P.tapsd, 0.f, 0, im.hmax, im.hist, P.nbins, tx, ty, sm);
+                const int gx = item.index % im.groups32_x, ty = item.index / im.groups32_x;
+                const int mode = item.kind == IT_GMAX ? GM_MAX : GM_HIST;
+                for (int tx = gx * kTilesPerItem; tx < min(im.tiles32_x, (gx + 1) * kTilesPerItem); ++tx) {
+                    if (P.tapsd.r == 3)
+                        gradient_tile<3>(mode, im.levels, nullptr, im.pitch, im.w, im.h, P.tapsd, 0.f, 0, im.hmax,
+                                         im.hist, P.nbins, tx, ty, sm);
+                    else
+                        gradient_tile<0>(mode, im.levels, nullptr, im.pitch, im.w, im.h, P.tapsd, 0.f, 0, im.hmax,
+                                         im.hist, P.nbins, tx, ty, sm);
+                }
                 slot = item.kind == IT_GMAX ? slot_gmax() : slot_ghist();
                 break;
             }
@@ -704,20 +938,26 @@ __global__ void __launch_bounds__(NT) k_batch(const __grid_constant__ BatchParam
                 slot = slot_pct();
                 break;
             case IT_COND: {
-                const int tx = item.index % im.tiles32_x, ty = item.index / im.tiles32_x;
+                const int gx = item.index % im.groups32_x, ty = item.index / im.groups32_x;
                 const float k = __ldcg(im.k);
-                gradient_tile(GM_COND, Lprev, im.g, im.pitch, im.w, im.h, P.tapsd, k, P.diffusivity, nullptr,
-                              nullptr, 0, tx, ty, sm);
+                for (int tx = gx * kTilesPerItem; tx < min(im.tiles32_x, (gx + 1) * kTilesPerItem); ++tx) {
+                    if (P.tapsd.r == 3)
+                        gradient_tile<3>(GM_COND, Lprev, im.g, im.pitch, im.w, im.h, P.tapsd, k, P.diffusivity,
+                                         nullptr, nullptr, 0, tx, ty, sm);
+                    else
+                        gradient_tile<0>(GM_COND, Lprev, im.g, im.pitch, im.w, im.h, P.tapsd, k, P.diffusivity,
+                                         nullptr, nullptr, 0, tx, ty, sm);
+                }
                 slot = slot_cond(lv);
                 break;
             }
             case IT_ROWS:
-                rows_item(im, Lprev, P.tau[lv], 4 * item.index, sm);
+                rows_dispatch(im, Lprev, P.tau[lv], 4 * item.index, sm);
                 slot = slot_rows(lv);
                 break;
             case IT_COLS:
-                cols_item(im, Lprev, im.levels + (size_t)lv * im.plane, P.tau[lv], P.cols * item.index, P.cols,
-                          sm);
+                cols_dispatch(im, Lprev, im.levels + (size_t)lv * im.plane, P.tau[lv], P.cols * item.index, P.cols,
+                              sm);
                 slot = slot_cols(lv);
                 break;
             case IT_DOH: {

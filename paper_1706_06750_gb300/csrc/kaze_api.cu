@@ -315,6 +315,39 @@ kaze_status run_detect_graph(kaze_handle* h, const float* d_img, int w, int hh, 
 
 }  // namespace
 
+// ------------------------------------------------- internal (batch API) ----
+
+namespace kz {
+
+// Enqueues the whole detection of one image on the handle's stream with the
+// levels, responses and keypoints going to caller-provided device buffers
+// (planes of the handle's pitch for w, packed); the handle lends only its
+// scratch (conductance, row solution, contrast statistics, status word).
+kaze_status handle_enqueue_into(kaze_handle* h, const float* d_img, int w, int hh, int pitch, float* levels,
+                                float* doh, kaze_keypoint* d_kp, unsigned int* d_count, int cap)
+{
+    KZ_CHECK(check_image(h, w, hh));
+    float* own_levels = h->levels;
+    float* own_doh = h->doh;
+    h->levels = levels;
+    h->doh = doh;
+    kaze_status s = enqueue_build(h, d_img, w, hh, pitch);
+    if (s == KAZE_OK) s = enqueue_response(h);
+    h->levels = own_levels;
+    h->doh = own_doh;
+    KZ_CHECK(s);
+    KZ_TRY(h, cudaMemsetAsync(d_count, 0, sizeof(unsigned int), h->stream));
+    KZ_LAUNCH(h, KK_EXTREMA, kz::launch_extrema(doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab,
+                                                h->opt.dthreshold, h->opt.edge_r, d_kp, cap, d_count, h->stream));
+    h->built = false;  // the handle's own buffers were not written
+    h->responded = false;
+    return KAZE_OK;
+}
+
+int* handle_status_ptr(kaze_handle* h) { return h->d_status; }
+
+}  // namespace kz
+
 // ------------------------------------------------------------------ ABI ----
 
 KAZE_API void kaze_default_options(kaze_options* o)

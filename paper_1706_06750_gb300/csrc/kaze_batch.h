@@ -11,13 +11,19 @@ namespace batch {
 
 constexpr int kBatchThreads = 256;  // threads per persistent CTA
 constexpr int kExtremaRows = 4;     // rows per extrema item
+constexpr int kTilesPerItem = 4;    // 32x32 stencil tiles per item (one tile row)
+
+// Chunk lengths for which the batch kernel carries compiled (register)
+// solvers; must match KZ_BATCH_ROW_M / KZ_BATCH_COL_M in k_batch.cu.
+constexpr int kRowCompiledM[] = {11, 21, 31};
+constexpr int kColCompiledM[] = {9, 13, 17, 19};
 
 enum ItemKind : uint8_t {
-    IT_PRESMOOTH = 0,  // 32x32 tile of L_0 = G_sigma0 * I
-    IT_GMAX,           // 32x32 tile of the gradient maximum
-    IT_GHIST,          // 32x32 tile of the gradient histogram
+    IT_PRESMOOTH = 0,  // kTilesPerItem 32x32 tiles of L_0 = G_sigma0 * I
+    IT_GMAX,           // ... of the gradient maximum
+    IT_GHIST,          // ... of the gradient histogram
     IT_PCT,            // percentile pick -> k (one per image)
-    IT_COND,           // 32x32 tile of the conductance of level `level`
+    IT_COND,           // ... of the conductance of level `level`
     IT_ROWS,           // 4 rows of the row solves of level `level`
     IT_COLS,           // strip of columns: column solves + average -> L_level
     IT_DOH,            // 64x64 tile of the response of level `level`
@@ -51,6 +57,7 @@ struct ImageDesc {
     int mcol;          // column chunk length (64 chunks, 4-column strips)
     int mcol32;        // column chunk length (32 chunks, 8-column strips)
     int tiles32_x, tiles64_x;
+    int groups32_x;    // items per tile row of the 32x32 stencils
 };
 
 struct BatchParams {
@@ -87,6 +94,7 @@ __host__ __device__ inline int slot_cols(int l) { return 6 + 3 * (l - 1); }
 __host__ __device__ inline int slot_doh(int l) { return 4 + 3 * (kMaxLevels - 1) + l; }
 __host__ __device__ inline int slot_extrema(int l) { return 4 + 3 * (kMaxLevels - 1) + kMaxLevels + l; }
 __host__ __device__ inline int slots_per_image() { return 4 + 3 * (kMaxLevels - 1) + 2 * kMaxLevels; }
+constexpr int kSlotWords = (4 + 3 * (kMaxLevels - 1) + 2 * kMaxLevels + 31) / 32;  // bit words per image
 
 cudaError_t configure_batch_kernel(int smem);
 cudaError_t batch_occupancy(int smem, int* blocks_per_sm);

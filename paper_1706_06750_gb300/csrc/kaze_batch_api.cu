@@ -38,7 +38,13 @@ struct kaze_batch {
     size_t stats_bytes = 0;
 
     kz::batch::BatchParams params;
-    kaze_batch_tuning tuning{4, 2};
+    kaze_batch_tuning tuning{KAZE_BATCH_PERSISTENT, 4, 2, 8};
+
+    // concurrent mode: single-image kernel sequences on parallel branches
+    std::vector<kaze_handle*> branch_h;
+    std::vector<cudaStream_t> branch_s;
+    std::vector<cudaEvent_t> branch_ev;  // [0] fork, [1..] joins
+    int* h_branch_status = nullptr;      // pinned, one word per branch
     int grid = 0, smem = 0;
     int n_items = 0;
     long long spin_limit = 1ll << 31;
@@ -98,12 +104,19 @@ int pool_floats(const kaze_batch* b, int cols)
     int smax = 1;
     for (int i = 0; i < b->N; ++i) smax = std::max(smax, b->params.tab.step[i]);
     need = std::max(need, (size_t)(64 + 4 * smax) * ((64 + 4 * smax) | 1));
+    auto in = [](int m, const int* set, int n) { return std::find(set, set + n, m) != set + n; };
     for (int i = 0; i < b->n; ++i) {
-        const int ls = (64 * odd_chunk(b->w[i], 64) + 3) / 4 * 4;
-        need = std::max(need, (size_t)4 * (3 * ls + 8 * 64));
+        // compiled solvers keep a' in registers (2 arrays), the run-time one
+        // in shared memory (3 arrays)
+        const int mr = odd_chunk(b->w[i], 64);
+        const int ra = in(mr, kRowCompiledM, 3) ? 2 : 3;
+        const int ls = (64 * mr + 3) / 4 * 4;
+        need = std::max(need, (size_t)4 * (ra * ls + 8 * 64));
         const int P = kBatchThreads / cols;
-        const int rs = P * odd_chunk(b->h[i], P);
-        need = std::max(need, (size_t)3 * rs * cols + (size_t)8 * P * cols);
+        const int mc = odd_chunk(b->h[i], P);
+        const int ca = (cols == 4 && in(mc, kColCompiledM, 4)) ? 2 : 3;
+        const int rs = P * mc;
+        need = std::max(need, (size_t)ca * rs * cols + (size_t)8 * P * cols);
     }
     return (int)need;
 }
@@ -120,7 +133,10 @@ void build_items(const kaze_batch* b, int cols, std::vector<Item>& items, std::v
         for (unsigned t = 0; t < count; ++t) items.push_back(Item{(uint8_t)kind, (uint8_t)level, (uint16_t)img, t});
         need[(size_t)img * S + slot] += count;
     };
-    auto t32 = [&](int i) { return (unsigned)(((b->w[i] + 31) / 32) * ((b->h[i] + 31) / 32)); };
+    auto t32 = [&](int i) {
+        const int tx = (b->w[i] + 31) / 32;
+        return (unsigned)(((tx + kTilesPerItem - 1) / kTilesPerItem) * ((b->h[i] + 31) / 32));
+    };
     auto t64 = [&](int i) { return (unsigned)(((b->w[i] + 63) / 64) * ((b->h[i] + 63) / 64)); };
     for (int i = 0; i < b->n; ++i) add(IT_PRESMOOTH, 0, i, t32(i), slot_presmooth());
     for (int i = 0; i < b->n; ++i) add(IT_GMAX, 0, i, t32(i), slot_gmax());
@@ -145,10 +161,51 @@ void drop_graph(kaze_batch* b)
     b->gexec = nullptr;
 }
 
+void drop_branches(kaze_batch* b)
+{
+    for (auto* h : b->branch_h) kaze_destroy(h);
+    for (auto s : b->branch_s) cudaStreamDestroy(s);
+    for (auto e : b->branch_ev) cudaEventDestroy(e);
+    b->branch_h.clear();
+    b->branch_s.clear();
+    b->branch_ev.clear();
+}
+
+// Concurrent mode: one single-image handle and stream per branch.
+kaze_status prepare_branches(kaze_batch* b)
+{
+    const int nb = std::max(1, std::min(b->tuning.streams, b->n));
+    if ((int)b->branch_h.size() == nb) return KAZE_OK;
+    drop_branches(b);
+    const int mw = *std::max_element(b->w.begin(), b->w.end());
+    const int mh = *std::max_element(b->h.begin(), b->h.end());
+    kaze_options o = b->opt;
+    o.max_keypoints = 1;  // keypoints go to the batch's own buffers
+    for (int i = 0; i < nb; ++i) {
+        cudaStream_t st = nullptr;
+        KB_TRY(b, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->branch_s.push_back(st);
+        kaze_handle* h = nullptr;
+        const kaze_status s = kaze_create(&o, mw, mh, st, &h);
+        if (s != KAZE_OK) return bfail(b, s, "branch handle creation failed");
+        b->branch_h.push_back(h);
+    }
+    for (int i = 0; i < nb + 1; ++i) {
+        cudaEvent_t e = nullptr;
+        KB_TRY(b, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->branch_ev.push_back(e);
+    }
+    return KAZE_OK;
+}
+
 // Prepares the work list, shared memory and grid for the current tuning.
 kaze_status prepare(kaze_batch* b)
 {
     using namespace kz::batch;
+    if (b->tuning.mode == KAZE_BATCH_CONCURRENT) {
+        drop_graph(b);
+        return prepare_branches(b);
+    }
     const int cols = b->tuning.cols_per_strip;
     std::vector<Item> items;
     std::vector<unsigned> need;
@@ -183,9 +240,38 @@ kaze_status prepare(kaze_batch* b)
     return KAZE_OK;
 }
 
+kaze_status enqueue_concurrent(kaze_batch* b)
+{
+    cudaStream_t st = b->stream;
+    const int nb = (int)b->branch_h.size();
+    KB_TRY(b, cudaMemsetAsync(b->d_count_status, 0, sizeof(unsigned) * (b->n + 1), st));
+    KB_TRY(b, cudaEventRecord(b->branch_ev[0], st));
+    for (int k = 0; k < nb; ++k) {
+        KB_TRY(b, cudaStreamWaitEvent(b->branch_s[k], b->branch_ev[0], 0));
+        KB_TRY(b, kaze_set_stream(b->branch_h[k], b->branch_s[k]) == KAZE_OK ? cudaSuccess : cudaErrorUnknown);
+    }
+    for (int i = 0; i < b->n; ++i) {
+        const ImageDesc& d = b->h_desc[i];
+        const kaze_status s = kz::handle_enqueue_into(b->branch_h[i % nb], d.img, d.w, d.h, d.img_pitch, d.levels,
+                                                      d.doh, d.kp, d.kp_count, d.kp_cap);
+        if (s != KAZE_OK)
+            return bfail(b, s, std::string("branch enqueue: ") + kaze_last_error(b->branch_h[i % nb]));
+    }
+    for (int k = 0; k < nb; ++k) {
+        KB_TRY(b, cudaMemcpyAsync(b->h_branch_status + k, kz::handle_status_ptr(b->branch_h[k]), sizeof(int),
+                                  cudaMemcpyDeviceToHost, b->branch_s[k]));
+        KB_TRY(b, cudaEventRecord(b->branch_ev[1 + k], b->branch_s[k]));
+        KB_TRY(b, cudaStreamWaitEvent(st, b->branch_ev[1 + k], 0));
+    }
+    KB_TRY(b, cudaMemcpyAsync(b->h_count_status, b->d_count_status, sizeof(unsigned) * (b->n + 1),
+                              cudaMemcpyDeviceToHost, st));
+    return KAZE_OK;
+}
+
 kaze_status enqueue(kaze_batch* b)
 {
     using namespace kz::batch;
+    if (b->tuning.mode == KAZE_BATCH_CONCURRENT) return enqueue_concurrent(b);
     cudaStream_t st = b->stream;
     KB_TRY(b, cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), st));
     KB_TRY(b, cudaMemsetAsync(b->d_done, 0, sizeof(unsigned) * (size_t)b->n * slots_per_image(), st));
@@ -325,7 +411,8 @@ KAZE_API kaze_status kaze_batch_create(const kaze_options* opt, int n, const int
     }
     char* a = (char*)b->arena;
     if (cudaMallocHost(&b->h_desc, sizeof(ImageDesc) * n) != cudaSuccess ||
-        cudaMallocHost(&b->h_count_status, sizeof(unsigned) * (n + 1)) != cudaSuccess) {
+        cudaMallocHost(&b->h_count_status, sizeof(unsigned) * (n + 1)) != cudaSuccess ||
+        cudaMallocHost(&b->h_branch_status, sizeof(int) * 64) != cudaSuccess) {
         kaze_batch_destroy(b);
         return KAZE_ERR_CUDA;
     }
@@ -365,6 +452,7 @@ KAZE_API kaze_status kaze_batch_create(const kaze_options* opt, int n, const int
         d.mcol = odd_chunk(h[i], 64);
         d.mcol32 = odd_chunk(h[i], 32);
         d.tiles32_x = (w[i] + 31) / 32;
+        d.groups32_x = (d.tiles32_x + kz::batch::kTilesPerItem - 1) / kz::batch::kTilesPerItem;
         d.tiles64_x = (w[i] + 63) / 64;
     }
     P.imgs = b->d_desc;
@@ -391,7 +479,10 @@ KAZE_API kaze_status kaze_batch_detect(kaze_batch* b, const float* const* d_imgs
     s = run(b);
     if (s != KAZE_OK) return s;
     KB_TRY(b, cudaStreamSynchronize(b->stream));
-    if (b->h_count_status[b->n]) return bfail(b, KAZE_ERR_TIMEOUT, "a bounded wait of the batched kernel ran out");
+    bool timed_out = b->h_count_status[b->n] != 0;
+    if (b->tuning.mode == KAZE_BATCH_CONCURRENT)
+        for (size_t k = 0; k < b->branch_h.size(); ++k) timed_out |= b->h_branch_status[k] != 0;
+    if (timed_out) return bfail(b, KAZE_ERR_TIMEOUT, "a bounded device-side wait ran out");
     kaze_status result = KAZE_OK;
     const unsigned cap = (unsigned)capacity_per_image;
     for (int i = 0; i < b->n; ++i) {
@@ -436,7 +527,9 @@ KAZE_API kaze_status kaze_batch_get_response(kaze_batch* b, int image, int level
 KAZE_API kaze_status kaze_batch_set_tuning(kaze_batch* b, const kaze_batch_tuning* t)
 {
     if (!b || !t) return KAZE_ERR_INVALID_ARG;
-    if ((t->cols_per_strip != 4 && t->cols_per_strip != 8) || t->ctas_per_sm < 1 || t->ctas_per_sm > 8)
+    if ((t->mode != KAZE_BATCH_PERSISTENT && t->mode != KAZE_BATCH_CONCURRENT) ||
+        (t->cols_per_strip != 4 && t->cols_per_strip != 8) || t->ctas_per_sm < 1 || t->ctas_per_sm > 8 ||
+        t->streams < 1 || t->streams > 64)
         return bfail(b, KAZE_ERR_INVALID_ARG, "tuning out of range");
     const kaze_batch_tuning old = b->tuning;
     b->tuning = *t;
@@ -467,11 +560,12 @@ KAZE_API kaze_status kaze_batch_autotune(kaze_batch* b, const float* const* d_im
     cudaEvent_t e0, e1;
     KB_TRY(b, cudaEventCreate(&e0));
     KB_TRY(b, cudaEventCreate(&e1));
-    const int cols_opts[2] = {4, 8};
-    const int cta_opts[2] = {1, 2};
-    for (int ci = 0; ci < 2; ++ci)
-        for (int ti = 0; ti < 2; ++ti) {
-            kaze_batch_tuning cand{cols_opts[ci], cta_opts[ti]};
+    std::vector<kaze_batch_tuning> cands;
+    for (int cols : {4, 8})
+        for (int ctas : {1, 2}) cands.push_back(kaze_batch_tuning{KAZE_BATCH_PERSISTENT, cols, ctas, 8});
+    for (int streams : {4, 8, 16}) cands.push_back(kaze_batch_tuning{KAZE_BATCH_CONCURRENT, 4, 2, streams});
+    for (const kaze_batch_tuning& cand : cands) {
+        {
             b->tuning = cand;
             if (prepare(b) != KAZE_OK) {
                 b->err.clear();
@@ -495,6 +589,7 @@ KAZE_API kaze_status kaze_batch_autotune(kaze_batch* b, const float* const* d_im
                 winner = cand;
             }
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->tuning = winner;
@@ -520,6 +615,8 @@ KAZE_API void kaze_batch_destroy(kaze_batch* b)
 {
     if (!b) return;
     drop_graph(b);
+    drop_branches(b);
+    if (b->h_branch_status) cudaFreeHost(b->h_branch_status);
     if (b->d_items) cudaFree(b->d_items);
     if (b->arena) cudaFree(b->arena);
     if (b->h_desc) cudaFreeHost(b->h_desc);

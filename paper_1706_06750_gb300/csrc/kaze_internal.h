@@ -103,4 +103,9 @@ cudaError_t launch_extrema(const float* D, int pitch, long long plane_stride, in
                            kaze_keypoint* d_kp, int cap, unsigned int* d_count,
                            cudaStream_t st);
 
+// Handle runtime helpers used by the batch API (kaze_api.cu).
+kaze_status handle_enqueue_into(kaze_handle* h, const float* d_img, int w, int hh, int pitch, float* levels,
+                                float* doh, kaze_keypoint* d_kp, unsigned int* d_count, int cap);
+int* handle_status_ptr(kaze_handle* h);
+
 }  // namespace kz

@@ -60,8 +60,13 @@ class Keypoint(ctypes.Structure):
     ]
 
 
+BATCH_PERSISTENT = 0
+BATCH_CONCURRENT = 1
+
+
 class BatchTuning(ctypes.Structure):
-    _fields_ = [("cols_per_strip", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+    _fields_ = [("mode", ctypes.c_int), ("cols_per_strip", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("streams", ctypes.c_int)]
 
 
 KEYPOINT_DTYPE = np.dtype([
@@ -546,12 +551,13 @@ class Batch:
         return torch.as_tensor(_DeviceView(p.value, h, w, pitch.value), device="cuda").clone()
 
     def tuning(self):
+        """(mode, cols_per_strip, ctas_per_sm, streams)"""
         t = BatchTuning()
         self._ck(self._L.kaze_batch_get_tuning(self._h, ctypes.byref(t)), "kaze_batch_get_tuning")
-        return (t.cols_per_strip, t.ctas_per_sm)
+        return (t.mode, t.cols_per_strip, t.ctas_per_sm, t.streams)
 
-    def set_tuning(self, cols_per_strip, ctas_per_sm):
-        t = BatchTuning(int(cols_per_strip), int(ctas_per_sm))
+    def set_tuning(self, mode=BATCH_PERSISTENT, cols_per_strip=4, ctas_per_sm=2, streams=8):
+        t = BatchTuning(int(mode), int(cols_per_strip), int(ctas_per_sm), int(streams))
         self._ck(self._L.kaze_batch_set_tuning(self._h, ctypes.byref(t)), "kaze_batch_set_tuning")
 
     def autotune(self, imgs, reps=3, cache=None):
@@ -579,7 +585,7 @@ class Batch:
         self._begin()
         self._ck(self._L.kaze_batch_autotune(self._h, ptrs, pitches, int(reps), ctypes.byref(best),
                                              ctypes.byref(ms)), "kaze_batch_autotune")
-        result = (best.cols_per_strip, best.ctas_per_sm)
+        result = (best.mode, best.cols_per_strip, best.ctas_per_sm, best.streams)
         if cache:
             try:
                 with open(cache) as f:
