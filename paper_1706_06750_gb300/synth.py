@@ -90,3 +90,14 @@ def batch_sizes(n: int = 64, seed: int = 4000):
 def batch_images(n: int = 64, seed: int = 4000):
     """The mixed-size batch: image j has seed 4000 + j."""
     return [image(w, h, seed + j) for j, (w, h) in enumerate(batch_sizes(n, seed))]
+
+
+def training_crop(j: int, size: int = 512) -> np.ndarray:
+    """Crop j of the learned surrogate's training set: a size x size window
+    of a 1920x1200 image of the recipe above (seed 5000 + j), at a position
+    drawn from ``default_rng(100000 + j)``."""
+    img = image(1920, 1200, 5000 + j)
+    rng = np.random.default_rng(100000 + j)
+    x0 = int(rng.integers(0, 1920 - size + 1))
+    y0 = int(rng.integers(0, 1200 - size + 1))
+    return np.ascontiguousarray(img[y0:y0 + size, x0:x0 + size])
