@@ -284,6 +284,105 @@ void kaze_batch_destroy(kaze_batch* b);
 kaze_status kaze_aos_step_static(const float* d_Lprev, const float* d_g, float* d_Lnext, int pitch, int w,
                                  int h_, float tau, void* cuda_stream);
 
+/* ---- learned AOS surrogate ---------------------------------------------- *
+ * Not in the paper: a small convolutional network that stands in for one
+ * AOS step of Eq. 4.  From the previous level L, its conductance g
+ * (Eq. 2-3, as kaze_op_conductance computes it) and the step
+ * tau = t_i - t_{i-1} (Eq. 7) it predicts the next level:
+ *   x0 = (dx, dy, g, s, c) per pixel: dx = 16 (L(x+1, y) - L(x, y)) and
+ *        dy = 16 (L(x, y+1) - L(x, y)) (0 in the last column / row),
+ *        s = log(1 + tau) / 5, c = 1; all zero outside the image.  L enters
+ *        through its differences only, as the AOS step commutes with adding
+ *        a constant to L;
+ *   h1 = relu(conv(x0)), h2 = relu(conv(h1)), h3 = relu(conv(h2)),
+ *   z = conv(h3), every conv 3x3 with zero padding and a bias, widths
+ *   5-32-32-32-1;  L_next = L + z / 256.
+ * Weights, every layer input (x0, h1, h2, h3) and every back-propagated
+ * layer gradient are BF16 (nearest, ties to even); biases are FP32; all sums
+ * are accumulated in FP32 on the tensor cores.  Training minimises the mean
+ * over all pixels of all samples of (L_next - T)^2 with Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8, bias-corrected) on FP32 master weights.  Training
+ * kernels add their partial sums in a fixed order: the same calls from the
+ * same state give bit-identical results, so a run resumed from a checkpoint
+ * repeats the uninterrupted one.
+ *
+ * Parameter vectors (KAZE_SURROGATE_PARAMS FP32 values, host memory): for
+ * each layer in order, W[out][3][3][in] (the two 3s: dy, dx = -1, 0, 1),
+ * then b[out].  Tap (dy, dx) of W multiplies the input at (x + dx, y + dy).
+ *
+ * Sample arrays: d_L[i], d_g[i], d_T[i], d_out[i] are DEVICE pointers to
+ * FP32 planes of w x h with the given pitch (elements); the arrays holding
+ * them and h_tau are HOST arrays of n entries, 1 <= n <=
+ * KAZE_SURROGATE_MAX_SAMPLES.  The sample table travels in the kernels'
+ * parameters, so steps can be recorded in a CUDA graph. */
+#define KAZE_SURROGATE_PARAMS 20257
+#define KAZE_SURROGATE_MAX_SAMPLES 64
+#define KAZE_SURROGATE_TRAIN 1   /* create flag: allocate training buffers      */
+#define KAZE_SURROGATE_FUSED 0   /* step path: whole network in one kernel     */
+#define KAZE_SURROGATE_LAYERED 1 /* step path: one kernel per layer (TRAIN)    */
+
+typedef struct kaze_surrogate kaze_surrogate;
+
+/* Creates a surrogate with seeded initial parameters: layers 1-3 uniform in
+ * +-sqrt(6 / (9 in)) from splitmix64 draws, the last layer and all biases 0
+ * (the untrained network returns L).  With KAZE_SURROGATE_TRAIN in flags it
+ * also allocates activations and gradients for max_samples images of up to
+ * max_w x max_h (about 440 bytes per pixel); without it the surrogate can
+ * only run the fused step, for any image size.  Returns KAZE_ERR_OOM or
+ * KAZE_ERR_INVALID_ARG (message: kaze_surrogate_last_error(NULL)). */
+kaze_status kaze_surrogate_create(int max_w, int max_h, int max_samples, int flags, unsigned long long seed,
+                                  void* cuda_stream, kaze_surrogate** out);
+kaze_status kaze_surrogate_set_stream(kaze_surrogate* s, void* cuda_stream);
+
+/* Copies the FP32 master parameters out / in (count must equal
+ * KAZE_SURROGATE_PARAMS).  set_params also zeroes the Adam moments and the
+ * step count.  Both synchronise the stream. */
+kaze_status kaze_surrogate_get_params(kaze_surrogate* s, float* h_params, int count);
+kaze_status kaze_surrogate_set_params(kaze_surrogate* s, const float* h_params, int count);
+
+/* d_out[i] = L_next of sample i (asynchronous).  path KAZE_SURROGATE_FUSED
+ * runs one persistent kernel; KAZE_SURROGATE_LAYERED runs the layer kernels
+ * of training (needs KAZE_SURROGATE_TRAIN and sizes within the maximum).
+ * d_out[i] must not overlap d_L[j] or d_g[j] (equal pointers are rejected). */
+kaze_status kaze_surrogate_step(kaze_surrogate* s, const float* const* d_L, const float* const* d_g,
+                                const float* h_tau, float* const* d_out, int n, int w, int h_, int pitch,
+                                int path);
+
+/* Loss and its gradient with respect to the parameters (h_grad: host,
+ * KAZE_SURROGATE_PARAMS values) for targets d_T; h_loss may be NULL.
+ * Parameters are not changed.  Synchronises. */
+kaze_status kaze_surrogate_gradients(kaze_surrogate* s, const float* const* d_L, const float* const* d_g,
+                                     const float* h_tau, const float* const* d_T, int n, int w, int h_,
+                                     int pitch, double* h_loss, float* h_grad);
+
+/* One Adam step with learning rate lr on the batch.  *h_loss (if h_loss is
+ * not NULL) receives the loss before the update, which synchronises. */
+kaze_status kaze_surrogate_train_step(kaze_surrogate* s, const float* const* d_L, const float* const* d_g,
+                                      const float* h_tau, const float* const* d_T, int n, int w, int h_,
+                                      int pitch, float lr, double* h_loss);
+kaze_status kaze_surrogate_steps_taken(const kaze_surrogate* s, long long* steps);
+
+/* Checkpoint: "KZSG", uint32 version 1, uint32 KAZE_SURROGATE_PARAMS,
+ * uint32 0, int64 steps taken, then parameters, Adam first and second
+ * moments (FP32, parameter-vector layout), all little-endian.  load
+ * restores all of it; a file that is not such a checkpoint gives
+ * KAZE_ERR_INVALID_ARG and leaves the surrogate unchanged. */
+kaze_status kaze_surrogate_save(kaze_surrogate* s, const char* path);
+kaze_status kaze_surrogate_load(kaze_surrogate* s, const char* path);
+
+/* Kernels the surrogate's last call enqueued; -1 for NULL. */
+int kaze_surrogate_last_launch_count(const kaze_surrogate* s);
+/* First error the surrogate recorded; with s == NULL, why the calling
+ * thread's last kaze_surrogate_create failed. */
+const char* kaze_surrogate_last_error(const kaze_surrogate* s);
+void kaze_surrogate_destroy(kaze_surrogate* s);
+
+/* Makes the handle's scale space evolve with the surrogate's fused step
+ * instead of the AOS row and column solves (s = NULL restores AOS, the
+ * default).  The surrogate is borrowed: keep it alive while it is set.
+ * Drops the handle's recorded detection graph. */
+kaze_status kaze_set_surrogate(kaze_handle* h, kaze_surrogate* s);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Number of kernel kinds the pipeline launches, and the name of kind k

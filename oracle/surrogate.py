@@ -12,17 +12,23 @@ Network contract (every choice below is a reading of the surrogate's
 one-line specification -- four 3x3 convolutions, 32 channels, BF16 weights,
 FP32 accumulation -- made concrete):
 
-* per-pixel inputs x0 = (L, g, s, c) with s = log(1 + tau) / 5 and c = 1;
-  outside the image every input is zero, so c marks where the image ends;
+* per-pixel inputs x0 = (dx, dy, g, s, c):
+  dx = 16 (L[y, x+1] - L[y, x]) (0 in the last column),
+  dy = 16 (L[y+1, x] - L[y, x]) (0 in the last row),
+  s = log(1 + tau) / 5 and c = 1; outside the image every input is zero, so
+  c marks where the image ends.  The level enters through its differences
+  only: the AOS step commutes with adding a constant to L (every row of the
+  operator A_l of Eq. 4 sums to zero), and BF16 holds small differences
+  precisely where it cannot resolve the step's changes on L itself;
 * h1 = relu(conv(x0; W1, b1)), h2 = relu(conv(h1; W2, b2)),
-  h3 = relu(conv(h2; W3, b3)), y = conv(h3; W4, b4), widths 4-32-32-32-1;
+  h3 = relu(conv(h2; W3, b3)), z = conv(h3; W4, b4), widths 5-32-32-32-1;
 * conv(x; W, b)[p, o] = b[o] + sum_{dy,dx in -1..1} sum_i
   W[o, dy+1, dx+1, i] x[p + (dy, dx), i], with x = 0 outside the image;
-* L_next = L + y;
+* L_next = L + z / 256;
 * loss = mean over all pixels of all samples of (L_next - T)^2.
 
 Storage precision (``bf16=True``): the weights, every layer input (x0, h1,
-h2, h3) and every back-propagated layer-output gradient (dy, dh3, dh2, dh1,
+h2, h3) and every back-propagated layer-output gradient (dz, dh3, dh2, dh1,
 taken after the ReLU mask) are rounded to bfloat16, round to nearest even;
 biases stay FP32.  Sums are exact here (FP64); the kernels accumulate in FP32.
 
@@ -39,7 +45,9 @@ from __future__ import annotations
 
 import numpy as np
 
-WIDTHS = (4, 32, 32, 32, 1)
+WIDTHS = (5, 32, 32, 32, 1)
+OUT_SCALE = 1.0 / 256.0   # L_next = L + OUT_SCALE z
+DIFF_SCALE = 16.0         # dx, dy = DIFF_SCALE x forward differences
 LAYERS = 4
 
 
@@ -114,15 +122,16 @@ def conv3x3_dw(dz, x):
 
 
 def features(L, g, tau):
-    """x0 [n, h, w, 4] from L, g [n, h, w] and tau [n]."""
+    """x0 [n, h, w, 5] from L, g [n, h, w] and tau [n]."""
     L = np.asarray(L, dtype=np.float64)
     g = np.asarray(g, dtype=np.float64)
     s = np.log1p(np.asarray(tau, dtype=np.float64)) / 5.0
-    x0 = np.empty(L.shape + (4,))
-    x0[..., 0] = L
-    x0[..., 1] = g
-    x0[..., 2] = s[:, None, None]
-    x0[..., 3] = 1.0
+    x0 = np.zeros(L.shape + (5,))
+    x0[:, :, :-1, 0] = DIFF_SCALE * (L[:, :, 1:] - L[:, :, :-1])
+    x0[:, :-1, :, 1] = DIFF_SCALE * (L[:, 1:, :] - L[:, :-1, :])
+    x0[..., 2] = g
+    x0[..., 3] = s[:, None, None]
+    x0[..., 4] = 1.0
     return x0
 
 
@@ -141,7 +150,7 @@ def forward(params, L, g, tau, bf16=True):
             acts.append(a)
         else:
             y = z[..., 0]
-    return L + y, {"layers": layers, "acts": acts, "bf16": bf16}
+    return L + OUT_SCALE * y, {"layers": layers, "acts": acts, "bf16": bf16}
 
 
 def loss(L_next, T):
@@ -155,7 +164,7 @@ def backward(params, L, g, tau, T, bf16=True):
     rnd = bf16_round if bf16 else (lambda a: a)
     layers, acts = cache["layers"], cache["acts"]
     e = L_next - np.asarray(T, dtype=np.float64)
-    dz = rnd((2.0 / e.size) * e)[..., None]      # dL/dy, one channel
+    dz = rnd((OUT_SCALE * 2.0 / e.size) * e)[..., None]   # dloss/dz, one channel
     grads = [None] * LAYERS
     for l in range(LAYERS - 1, -1, -1):
         W, _ = layers[l]

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "kaze_internal.h"
+#include "surrogate.h"
 
 #define KAZE_API extern "C" __attribute__((visibility("default")))
 
@@ -24,11 +25,11 @@ namespace {
 // Kernel kinds, in pipeline order, for launch counting and profiling.
 enum KernelKind {
     KK_PRESMOOTH = 0, KK_GRAD_MAX, KK_GRAD_HIST, KK_PERCENTILE, KK_SET_SCALAR,
-    KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_COUNT
+    KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_SURROGATE, KK_COUNT
 };
 const char* const kKindNames[KK_COUNT] = {
     "presmooth", "grad_max", "grad_hist", "percentile", "set_scalar",
-    "conductance", "aos_rows", "aos_cols", "doh", "extrema"};
+    "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate"};
 }  // namespace
 
 struct kaze_handle {
@@ -63,6 +64,10 @@ struct kaze_handle {
     double t[kz::kMaxLevels];
     kz::GaussTaps taps0, tapsd;
     kz::LevelTable tab;
+
+    // learned stand-in for the AOS step (borrowed; NULL: AOS)
+    const kaze_surrogate* surrogate = nullptr;
+    float sg_s[kz::kMaxLevels];  // BF16 value of log(1 + tau_i) / 5 per level
 
     // recorded detection graph
     cudaGraphExec_t gexec = nullptr;
@@ -207,6 +212,21 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
         float* Li = level_ptr(h, i);
         const float tau = (float)(h->t[i] - h->t[i - 1]);
         KZ_LAUNCH(h, KK_CONDUCTANCE, kz::launch_conductance(Lp, h->g, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
+        if (h->surrogate) {
+            kz::sg::Samples S;
+            std::memset(&S, 0, sizeof(S));
+            S.L[0] = Lp;
+            S.g[0] = h->g;
+            S.out[0] = Li;
+            S.s[0] = h->sg_s[i];
+            S.n = 1;
+            S.w = w;
+            S.h = hh;
+            S.pitch = P;
+            S.opitch = P;
+            KZ_LAUNCH(h, KK_SURROGATE, kz::sg::enqueue_pipeline_step(h->surrogate, S, st));
+            continue;
+        }
         KZ_LAUNCH(h, KK_AOS_ROWS, kz::launch_aos_rows(Lp, h->g, h->ux, P, w, hh, tau, h->d_status, st));
         KZ_LAUNCH(h, KK_AOS_COLS, kz::launch_aos_cols(Lp, h->g, h->ux, Li, P, w, hh, tau, h->d_status, st));
     }
@@ -681,6 +701,20 @@ KAZE_API kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch
     for (int i = 0; i < n; ++i) t.sigma[i] = h_sigma[i];
     KZ_CHECK(enqueue_extrema(h, d_D, pitch, plane_stride, w, hh, n, t));
     return collect_keypoints(h, h_out, capacity, count);
+}
+
+KAZE_API kaze_status kaze_set_surrogate(kaze_handle* h, kaze_surrogate* s)
+{
+    if (!h) return KAZE_ERR_INVALID_ARG;
+    drop_graph(h);
+    h->surrogate = s;
+    if (s) {
+        for (int i = 1; i < h->N; ++i)
+            h->sg_s[i] = kz::sg::input_scale(h->t[i] - h->t[i - 1]);
+    }
+    h->built = false;
+    h->responded = false;
+    return KAZE_OK;
 }
 
 KAZE_API int kaze_kernel_kinds(void) { return KK_COUNT; }

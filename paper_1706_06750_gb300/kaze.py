@@ -115,6 +115,24 @@ _SIGNATURES = {
     "kaze_batch_set_wait_limit": (_i, [_vp, ctypes.c_longlong, _i]),
     "kaze_batch_last_error": (ctypes.c_char_p, [_vp]),
     "kaze_batch_destroy": (None, [_vp]),
+    "kaze_surrogate_create": (_i, [_i, _i, _i, _i, ctypes.c_ulonglong, _vp, ctypes.POINTER(_vp)]),
+    "kaze_surrogate_set_stream": (_i, [_vp, _vp]),
+    "kaze_surrogate_get_params": (_i, [_vp, ctypes.POINTER(_f), _i]),
+    "kaze_surrogate_set_params": (_i, [_vp, ctypes.POINTER(_f), _i]),
+    "kaze_surrogate_step": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_f),
+                                 ctypes.POINTER(_vp), _i, _i, _i, _i, _i]),
+    "kaze_surrogate_gradients": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_f),
+                                      ctypes.POINTER(_vp), _i, _i, _i, _i, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(_f)]),
+    "kaze_surrogate_train_step": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_f),
+                                       ctypes.POINTER(_vp), _i, _i, _i, _i, _f, ctypes.POINTER(ctypes.c_double)]),
+    "kaze_surrogate_steps_taken": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "kaze_surrogate_save": (_i, [_vp, ctypes.c_char_p]),
+    "kaze_surrogate_load": (_i, [_vp, ctypes.c_char_p]),
+    "kaze_surrogate_last_launch_count": (_i, [_vp]),
+    "kaze_surrogate_last_error": (ctypes.c_char_p, [_vp]),
+    "kaze_surrogate_destroy": (None, [_vp]),
+    "kaze_set_surrogate": (_i, [_vp, _vp]),
     "kaze_kernel_kinds": (_i, []),
     "kaze_kernel_name": (ctypes.c_char_p, [_i]),
     "kaze_last_launch_count": (_i, [_vp]),
@@ -366,6 +384,14 @@ class Kaze:
         return _sorted_keypoints(buf, min(n.value, cap))
 
     # -- instrumentation --
+    def set_surrogate(self, surrogate):
+        """Evolve the scale space with the learned surrogate's fused step
+        instead of AOS (None restores AOS).  The Surrogate must outlive its
+        use here."""
+        self._ck(self._L.kaze_set_surrogate(self._h, surrogate._s if surrogate is not None else None),
+                 "kaze_set_surrogate")
+        self._surrogate = surrogate
+
     def last_launch_count(self):
         return int(self._L.kaze_last_launch_count(self._h))
 
@@ -604,3 +630,165 @@ class Batch:
         exists, so the next detect reports ERR_TIMEOUT."""
         self._ck(self._L.kaze_batch_set_wait_limit(self._h, int(cycles), int(stall_image)),
                  "kaze_batch_set_wait_limit")
+
+
+SURROGATE_PARAMS = 20257
+SURROGATE_MAX_SAMPLES = 64
+SURROGATE_TRAIN = 1
+SURROGATE_FUSED = 0
+SURROGATE_LAYERED = 1
+
+
+def _planes(x, name):
+    """A list of 2-D float32 CUDA tensors (or one 3-D tensor [n, h, w]) ->
+    (n, w, h, pitch, ctypes array of device pointers).  Every plane must
+    share shape and row pitch."""
+    import torch
+    if isinstance(x, torch.Tensor) and x.dim() == 3:
+        x = [x[i] for i in range(x.shape[0])]
+    elif isinstance(x, torch.Tensor):
+        x = [x]
+    if not x:
+        raise KazeError(ERR_INVALID_ARG, f"{name}: no planes")
+    geo = None
+    for t in x:
+        g = _check_image(t)
+        if geo is not None and g != geo:
+            raise KazeError(ERR_INVALID_ARG, f"{name}: planes differ in shape or pitch")
+        geo = g
+    arr = (_vp * len(x))(*[t.data_ptr() for t in x])
+    return len(x), geo[0], geo[1], geo[2], arr
+
+
+class Surrogate:
+    """The learned stand-in for one AOS step (kaze_surrogate_*): a 4-layer
+    3x3 convolutional network, BF16 weights, FP32 accumulation."""
+
+    def __init__(self, max_w=0, max_h=0, max_samples=0, train=False, seed=0, stream=None):
+        import torch
+        self._L = lib()
+        if stream is None:
+            stream = torch.cuda.Stream()
+        self._stream = stream
+        s = _vp()
+        st = self._L.kaze_surrogate_create(int(max_w), int(max_h), int(max_samples),
+                                           SURROGATE_TRAIN if train else 0, int(seed),
+                                           _vp(stream.cuda_stream), ctypes.byref(s))
+        if st != OK:
+            raise KazeError(st, f"kaze_surrogate_create failed: {self._L.kaze_status_string(st).decode()}: "
+                                f"{self._L.kaze_surrogate_last_error(None).decode()}")
+        self._s = s
+
+    def _ck(self, st, what):
+        if st != OK:
+            msg = self._L.kaze_surrogate_last_error(self._s).decode()
+            raise KazeError(st, f"{what}: {self._L.kaze_status_string(st).decode()}: {msg}")
+        return st
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._L.kaze_surrogate_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def _begin(self):
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur != self._stream:
+            self._stream.wait_stream(cur)
+
+    def _end(self):
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur != self._stream:
+            cur.wait_stream(self._stream)
+
+    def _batch(self, L, g, tau, T=None):
+        n, w, h, pitch, pl = _planes(L, "L")
+        ng, wg, hg, pg, pg_arr = _planes(g, "g")
+        if (ng, wg, hg, pg) != (n, w, h, pitch):
+            raise KazeError(ERR_INVALID_ARG, "g must match L")
+        taus = np.broadcast_to(np.asarray(tau, dtype=np.float32), (n,)).copy()
+        ta = taus.ctypes.data_as(ctypes.POINTER(_f))
+        pt = None
+        if T is not None:
+            nt, wt, ht, ptc, pt = _planes(T, "T")
+            if (nt, wt, ht, ptc) != (n, w, h, pitch):
+                raise KazeError(ERR_INVALID_ARG, "T must match L")
+        return n, w, h, pitch, pl, pg_arr, taus, ta, pt
+
+    def step(self, L, g, tau, out, path=SURROGATE_FUSED):
+        """out[i] = L_next of (L[i], g[i], tau[i]); asynchronous."""
+        n, w, h, pitch, pl, pg, taus, ta, _ = self._batch(L, g, tau)
+        no, wo, ho, po, pout = _planes(out, "out")
+        if (no, wo, ho, po) != (n, w, h, pitch):
+            raise KazeError(ERR_INVALID_ARG, "out must match L")
+        self._begin()
+        self._ck(self._L.kaze_surrogate_step(self._s, pl, pg, ta, pout, n, w, h, pitch, int(path)),
+                 "kaze_surrogate_step")
+        self._end()
+
+    def gradients(self, L, g, tau, T):
+        """(loss, gradient) of the mean squared error against T."""
+        n, w, h, pitch, pl, pg, taus, ta, pt = self._batch(L, g, tau, T)
+        grad = np.zeros(SURROGATE_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        self._begin()
+        self._ck(self._L.kaze_surrogate_gradients(self._s, pl, pg, ta, pt, n, w, h, pitch, ctypes.byref(loss),
+                                                  grad.ctypes.data_as(ctypes.POINTER(_f))),
+                 "kaze_surrogate_gradients")
+        self._end()
+        return float(loss.value), grad
+
+    def train_step(self, L, g, tau, T, lr, want_loss=True):
+        """One Adam step; returns the loss before it (None if not wanted)."""
+        n, w, h, pitch, pl, pg, taus, ta, pt = self._batch(L, g, tau, T)
+        loss = ctypes.c_double(0.0)
+        self._begin()
+        self._ck(self._L.kaze_surrogate_train_step(self._s, pl, pg, ta, pt, n, w, h, pitch, float(lr),
+                                                   ctypes.byref(loss) if want_loss else None),
+                 "kaze_surrogate_train_step")
+        self._end()
+        return float(loss.value) if want_loss else None
+
+    def params(self):
+        p = np.zeros(SURROGATE_PARAMS, dtype=np.float32)
+        self._ck(self._L.kaze_surrogate_get_params(self._s, p.ctypes.data_as(ctypes.POINTER(_f)), p.size),
+                 "kaze_surrogate_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.shape != (SURROGATE_PARAMS,):
+            raise KazeError(ERR_INVALID_ARG, f"expected {SURROGATE_PARAMS} parameters")
+        self._ck(self._L.kaze_surrogate_set_params(self._s, p.ctypes.data_as(ctypes.POINTER(_f)), p.size),
+                 "kaze_surrogate_set_params")
+
+    def steps_taken(self):
+        n = ctypes.c_longlong(0)
+        self._ck(self._L.kaze_surrogate_steps_taken(self._s, ctypes.byref(n)), "kaze_surrogate_steps_taken")
+        return int(n.value)
+
+    def save(self, path):
+        self._ck(self._L.kaze_surrogate_save(self._s, os.fsencode(path)), "kaze_surrogate_save")
+
+    def load(self, path):
+        self._ck(self._L.kaze_surrogate_load(self._s, os.fsencode(path)), "kaze_surrogate_load")
+
+    def last_launch_count(self):
+        return int(self._L.kaze_surrogate_last_launch_count(self._s))

@@ -1,0 +1,296 @@
+"""GPU parity of the learned AOS surrogate (kaze_surrogate_*) against the FP64
+oracle of oracle/surrogate.py, which models the same BF16 storage points.
+
+Tolerances.  The kernels and the oracle see bit-identical BF16 inputs and
+weights; they differ in the sums only (FP32 on the tensor cores, exact in the
+oracle), relative error about 1e-6 of the sum of absolute terms.  Where such
+a sum lands next to a BF16 rounding boundary of the next layer's input the two
+round to neighbouring values, one BF16 unit (2^-8 relative) apart, and the
+difference travels on through the remaining layers.  So every output is
+compared against M, the oracle's sum of absolute contributions to it
+(sum |W| |x| + |b| of its last layer, / 256): |gpu - oracle| <= 2^-6 M everywhere
+(a wrong tap, channel or sign would be of order M), and the median
+|gpu - oracle| / M must stay below 2^-12 (most outputs see no flip at all)."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import surrogate as so
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_06750_gb300 import build, kaze
+    build.build()
+    return kaze
+
+
+def random_params(seed, last_scale=1.0):
+    r = np.random.default_rng(seed)
+    layers = []
+    for l, (ws, bs) in enumerate(so.layer_shapes()):
+        fan_in = ws[1] * ws[2] * ws[3]
+        s = np.sqrt(2.0 / fan_in) * (last_scale if l == 3 else 1.0)
+        layers.append((r.standard_normal(ws) * s, r.standard_normal(bs) * 0.05))
+    return so.pack(layers).astype(np.float32).astype(np.float64)
+
+
+def sample_inputs(seed, n, h, w):
+    r = np.random.default_rng(seed)
+    L = r.uniform(0, 1, (n, h, w)).astype(np.float32)
+    g = r.uniform(0.02, 1, (n, h, w)).astype(np.float32)
+    tau = r.uniform(0.3, 40.0, n).astype(np.float32)
+    T = (L + 0.05 * r.standard_normal((n, h, w))).astype(np.float32)
+    return L, g, tau, T
+
+
+def out_magnitude(params, L, g, tau):
+    """M: (sum of |W4| |h3| + |b4|) / 256 per output pixel, from the oracle."""
+    _, cache = so.forward(params, L, g, tau, bf16=True)
+    W4, b4 = cache["layers"][3]
+    return so.OUT_SCALE * so.conv3x3(np.abs(cache["acts"][3]), np.abs(W4), np.abs(b4))[..., 0]
+
+
+def dev(a, pitch=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    if pitch is None:
+        return t
+    n, h, w = t.shape
+    buf = torch.full((n, h, pitch), float("nan"), device="cuda")
+    buf[:, :, :w] = t
+    return buf[:, :, :w]
+
+
+def check_close(got, want, M, what):
+    d = np.abs(got.astype(np.float64) - want)
+    assert np.all(np.isfinite(got)), what
+    worst = float(np.max(d / (M + 1e-30)))
+    assert np.all(d <= 2.0 ** -6 * M + 1e-7), (what, worst)
+    assert float(np.median(d / (M + 1e-30))) <= 2.0 ** -12, what
+
+
+@pytest.mark.parametrize("n,h,w,pitch", [(3, 29, 37, 40), (1, 45, 70, 96), (2, 16, 16, 16), (1, 3, 5, 8)])
+@pytest.mark.parametrize("path", ["fused", "layered"])
+def test_forward_matches_oracle(K, n, h, w, pitch, path):
+    params = random_params(11)
+    L, g, tau, _ = sample_inputs(12, n, h, w)
+    s = K.Surrogate(80, 48, 3, train=True)
+    s.set_params(params.astype(np.float32))
+    dL, dg = dev(L, pitch), dev(g, pitch)
+    out = dev(np.full((n, h, w), np.nan, np.float32), pitch)
+    s.step(dL, dg, tau, out, path=K.SURROGATE_FUSED if path == "fused" else K.SURROGATE_LAYERED)
+    torch.cuda.synchronize()
+    want, _ = so.forward(params, L.astype(np.float64), g.astype(np.float64), tau.astype(np.float64), bf16=True)
+    check_close(out.cpu().numpy(), want, out_magnitude(params, L, g, tau), f"{path} {n}x{h}x{w}")
+    # pitch padding untouched
+    full = out.as_strided((n, h, pitch), (h * pitch, pitch, 1)).cpu().numpy()
+    assert np.all(np.isnan(full[:, :, w:]))
+    assert s.last_launch_count() == (1 if path == "fused" else 5)
+
+
+def test_fused_and_layered_agree_bitwise(K):
+    params = random_params(13)
+    L, g, tau, _ = sample_inputs(14, 4, 61, 83)
+    s = K.Surrogate(83, 61, 4, train=True)
+    s.set_params(params.astype(np.float32))
+    dL, dg = dev(L), dev(g)
+    a = torch.empty_like(dL)
+    b = torch.empty_like(dL)
+    s.step(dL, dg, tau, a, path=K.SURROGATE_FUSED)
+    s.step(dL, dg, tau, b, path=K.SURROGATE_LAYERED)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_untrained_network_is_the_identity(K):
+    L, g, tau, _ = sample_inputs(15, 2, 33, 47)
+    s = K.Surrogate(seed=3)
+    dL, dg = dev(L), dev(g)
+    out = torch.empty_like(dL)
+    s.step(dL, dg, tau, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, dL)
+    p = s.params()
+    # seeded init: hidden weights uniform within +-sqrt(6 / fan_in), last layer and biases zero
+    layers = so.unpack(p.astype(np.float64))
+    for l, (W, b) in enumerate(layers):
+        assert np.all(b == 0)
+        if l < 3:
+            bound = np.sqrt(6.0 / (9 * W.shape[3]))
+            assert 0.9 * bound < np.max(np.abs(W)) <= bound
+        else:
+            assert np.all(W == 0)
+    np.testing.assert_array_equal(K.Surrogate(seed=3).params(), p)
+    assert not np.array_equal(K.Surrogate(seed=4).params(), p)
+
+
+def grad_magnitude(params, L, g, tau, T):
+    """Per-parameter sum of |dz| |x| (weights) and |dz| (biases) of the
+    oracle's backward pass: the scale of each gradient entry."""
+    L_next, cache = so.forward(params, L, g, tau, bf16=True)
+    layers, acts = cache["layers"], cache["acts"]
+    e = L_next - T
+    dz = so.bf16_round((so.OUT_SCALE * 2.0 / e.size) * e)[..., None]
+    mags = [None] * 4
+    for l in range(3, -1, -1):
+        W, _ = layers[l]
+        mags[l] = so.conv3x3_dw(np.abs(dz), np.abs(acts[l]))
+        if l > 0:
+            dz = so.bf16_round(so.conv3x3_dx(dz, W) * (acts[l] > 0))
+    return so.pack(mags)
+
+
+def test_gradients_match_oracle(K):
+    params = random_params(21, last_scale=0.5)
+    n, h, w = 2, 33, 40
+    L, g, tau, T = sample_inputs(22, n, h, w)
+    s = K.Surrogate(w, h, n, train=True)
+    s.set_params(params.astype(np.float32))
+    loss, grad = s.gradients(dev(L), dev(g), tau, dev(T))
+    args = (L.astype(np.float64), g.astype(np.float64), tau.astype(np.float64), T.astype(np.float64))
+    want_loss, want = so.backward(params, *args, bf16=True)
+    assert abs(loss - want_loss) <= 1e-5 * want_loss
+    M = grad_magnitude(params, *args)
+    d = np.abs(grad.astype(np.float64) - want)
+    assert np.all(d <= 2.0 ** -6 * M + 1e-12), float(np.max(d / (M + 1e-30)))
+    o = 0
+    for ws, bs in so.layer_shapes():
+        k = int(np.prod(ws)) + int(np.prod(bs))
+        rel = np.linalg.norm(grad[o:o + k] - want[o:o + k]) / np.linalg.norm(want[o:o + k])
+        assert rel < 1e-3, (o, rel)
+        o += k
+    assert s.last_launch_count() == 18
+
+
+def test_train_step_is_adam_on_the_oracle_gradient(K):
+    params = random_params(31, last_scale=0.5)
+    n, h, w = 2, 24, 30
+    L, g, tau, T = sample_inputs(32, n, h, w)
+    s = K.Surrogate(w, h, n, train=True)
+    s.set_params(params.astype(np.float32))
+    lr = 1e-3
+    loss = s.train_step(dev(L), dev(g), tau, dev(T), lr)
+    p1 = s.params().astype(np.float64)
+    args = (L.astype(np.float64), g.astype(np.float64), tau.astype(np.float64), T.astype(np.float64))
+    want_loss, grad = so.backward(params, *args, bf16=True)
+    assert abs(loss - want_loss) <= 1e-5 * want_loss
+    want, _, _ = so.adam(params, grad, np.zeros_like(params), np.zeros_like(params), 1, lr)
+    d = np.abs(p1 - want)
+    # the first Adam step moves each parameter by lr g / (|g| + eps): the
+    # same as the oracle's unless g is so small that FP32 rounding decides
+    # its sign or size
+    assert np.all(d <= 2 * lr + 1e-6)
+    assert np.mean(d > 0.01 * lr) < 0.005
+    assert s.steps_taken() == 1
+    assert s.last_launch_count() == 19
+
+
+def test_checkpoint_resume_is_bit_identical(K):
+    n, h, w = 3, 40, 52
+    L, g, tau, T = sample_inputs(41, n, h, w)
+    dL, dg, dT = dev(L), dev(g), dev(T)
+    a = K.Surrogate(w, h, n, train=True, seed=7)
+    for _ in range(3):
+        a.train_step(dL, dg, tau, dT, 2e-3, want_loss=False)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "s.ckpt")
+        a.save(path)
+        assert os.path.getsize(path) == 4 + 12 + 8 + 3 * 4 * K.SURROGATE_PARAMS
+        la = a.train_step(dL, dg, tau, dT, 2e-3)
+        pa = a.params()
+        b = K.Surrogate(w, h, n, train=True, seed=99)
+        b.load(path)
+        assert b.steps_taken() == 3
+        lb = b.train_step(dL, dg, tau, dT, 2e-3)
+        assert la == lb
+        np.testing.assert_array_equal(b.params(), pa)
+        assert b.steps_taken() == 4
+        bad = os.path.join(d, "bad.ckpt")
+        with open(bad, "wb") as f:
+            f.write(b"KZSG" + bytes(20))
+        with pytest.raises(K.KazeError):
+            b.load(bad)
+        np.testing.assert_array_equal(b.params(), pa)
+
+
+def test_training_on_oracle_pairs_reduces_the_loss(K, oracle_mod):
+    from paper_1706_06750_gb300 import synth
+    opt = oracle_mod.Options.make(octaves=2, sublevels=2)
+    _, t = oracle_mod.scale_table(2, 2, 1.6)
+    Ls, gs, taus, Ts = [], [], [], []
+    for j in range(3):
+        img = synth.image(64, 48, 5000 + j)
+        levels, k = oracle_mod.build_scale_space(img, opt)
+        for i in range(len(levels) - 1):
+            Ls.append(levels[i])
+            gs.append(oracle_mod.conductance(levels[i], k))
+            taus.append(t[i + 1] - t[i])
+            Ts.append(levels[i + 1])
+    L = np.array(Ls, np.float32)
+    g = np.array(gs, np.float32)
+    T = np.array(Ts, np.float32)
+    tau = np.array(taus, np.float32)
+    s = K.Surrogate(64, 48, len(Ls), train=True, seed=1)
+    dL, dg, dT = dev(L), dev(g), dev(T)
+    first = s.train_step(dL, dg, tau, dT, 3e-3)
+    # the untrained network is the identity: its loss is the mean square of the step
+    assert abs(first - float(np.mean((T.astype(np.float64) - L) ** 2))) <= 1e-5 * first
+    for _ in range(150):
+        last = s.train_step(dL, dg, tau, dT, 3e-3)
+    assert last < 0.5 * first, (first, last)
+
+
+def test_pipeline_uses_the_surrogate(K):
+    from paper_1706_06750_gb300 import synth
+    img = torch.from_numpy(synth.image(96, 80, 77)).cuda()
+    kz = K.Kaze(96, 80, octaves=2, sublevels=2)
+    s = K.Surrogate(seed=5)
+    kz.set_surrogate(s)
+    kz.build_scale_space(img)
+    levels = [kz.level(i) for i in range(kz.n_levels)]
+    # untrained surrogate: every level equals L_0
+    for i in range(1, kz.n_levels):
+        assert torch.equal(levels[i], levels[0])
+    # a random network: level i is the surrogate step of level i - 1 with
+    # its conductance, exactly as the standalone calls compute it
+    s.set_params(random_params(51, last_scale=0.1).astype(np.float32))
+    kz.build_scale_space(img)
+    k = kz.contrast()
+    for i in range(1, kz.n_levels):
+        prev = kz.level(i - 1)
+        g = torch.empty_like(prev)
+        kz.op_conductance(prev, g, k)
+        want = torch.empty_like(prev)
+        s.step(prev, g, [kz.level_time(i) - kz.level_time(i - 1)], want)
+        torch.cuda.synchronize()
+        assert torch.equal(kz.level(i), want), i
+    names = [K.lib().kaze_kernel_name(j).decode() for j in range(K.lib().kaze_kernel_kinds())]
+    assert "surrogate" in names
+    kz.set_surrogate(None)
+    kz.build_scale_space(img)
+    assert not torch.equal(kz.level(3), kz.level(0))
+
+
+def test_invalid_arguments(K):
+    s = K.Surrogate(32, 32, 2, train=True)
+    x = torch.rand(2, 16, 16, device="cuda")
+    with pytest.raises(K.KazeError):
+        s.step(x, x, [1.0, 1.0], x)  # output aliases an input
+    big = torch.rand(3, 16, 16, device="cuda")
+    with pytest.raises(K.KazeError):
+        s.step(big, big, [1.0] * 3, torch.empty_like(big), path=K.SURROGATE_LAYERED)  # n > max_samples
+    with pytest.raises(K.KazeError):
+        s.step(x, x, [-1.0, 1.0], torch.empty_like(x))  # negative tau
+    inf = K.Surrogate()
+    with pytest.raises(K.KazeError) as e:
+        inf.step(x, x, [1.0, 1.0], torch.empty_like(x), path=K.SURROGATE_LAYERED)
+    assert e.value.status == K.ERR_STATE
+    with pytest.raises(K.KazeError):
+        inf.set_params(np.full(K.SURROGATE_PARAMS, np.nan, np.float32))

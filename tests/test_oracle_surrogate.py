@@ -14,12 +14,12 @@ def _rng(seed):
 
 
 def test_param_count_and_layout():
-    # widths 4-32-32-32-1 with 3x3 kernels and biases
-    assert so.PARAM_COUNT == 32 * 9 * 4 + 32 + 32 * 9 * 32 + 32 + 32 * 9 * 32 + 32 + 1 * 9 * 32 + 1
+    # widths 5-32-32-32-1 with 3x3 kernels and biases
+    assert so.PARAM_COUNT == 32 * 9 * 5 + 32 + 32 * 9 * 32 + 32 + 32 * 9 * 32 + 32 + 1 * 9 * 32 + 1
     p = np.arange(so.PARAM_COUNT, dtype=np.float64)
     np.testing.assert_array_equal(so.pack(so.unpack(p)), p)
     (W1, b1), *_ = so.unpack(p)
-    assert W1.shape == (32, 3, 3, 4) and b1[0] == 32 * 9 * 4
+    assert W1.shape == (32, 3, 3, 5) and b1[0] == 32 * 9 * 5
 
 
 def test_bf16_round_matches_torch():
@@ -70,18 +70,23 @@ def test_conv_backward_is_the_adjoint():
 
 
 def _hand_built_params(alpha, beta, gamma, delta, eps, bias):
-    """A network whose output is y = alpha L(y, x+1) - beta L(y-1, x)
-    + gamma g + delta s + eps c + bias, with zero outside the image."""
+    """A network whose raw output is z = alpha dx(y, x+1) - beta dy(y-1, x)
+    + gamma g + delta s + eps c + bias, with zero outside the image: the
+    signed differences pass the ReLUs as positive and negative parts."""
     layers = [(np.zeros(ws), np.zeros(bs)) for ws, bs in so.layer_shapes()]
-    for l in range(3):  # channels 0..3 carry L, g, s, c through the ReLUs
-        for ch in range(4):
+    W1 = layers[0][0]
+    W1[0, 1, 1, 0], W1[1, 1, 1, 0] = 1.0, -1.0   # dx+, dx-
+    W1[2, 1, 1, 1], W1[3, 1, 1, 1] = 1.0, -1.0   # dy+, dy-
+    W1[4, 1, 1, 2] = W1[5, 1, 1, 3] = W1[6, 1, 1, 4] = 1.0  # g, s, c
+    for l in (1, 2):
+        for ch in range(7):
             layers[l][0][ch, 1, 1, ch] = 1.0
     W4, b4 = layers[3]
-    W4[0, 1, 2, 0] = alpha        # tap (dy, dx) = (0, +1)
-    W4[0, 0, 1, 0] = -beta        # tap (dy, dx) = (-1, 0)
-    W4[0, 1, 1, 1] = gamma
-    W4[0, 1, 1, 2] = delta
-    W4[0, 1, 1, 3] = eps
+    W4[0, 1, 2, 0], W4[0, 1, 2, 1] = alpha, -alpha     # tap (dy, dx) = (0, +1)
+    W4[0, 0, 1, 2], W4[0, 0, 1, 3] = -beta, beta       # tap (dy, dx) = (-1, 0)
+    W4[0, 1, 1, 4] = gamma
+    W4[0, 1, 1, 5] = delta
+    W4[0, 1, 1, 6] = eps
     b4[0] = bias
     return so.pack(layers)
 
@@ -97,13 +102,28 @@ def test_forward_matches_closed_form(bf16):
     p = _hand_built_params(a, b_, c, d, e, bias)
     got, _ = so.forward(p, L, g, tau, bf16=bf16)
     q = so.bf16_round if bf16 else (lambda v: v)
-    Lq, gq, sq = q(L), q(g), q(np.log1p(tau) / 5.0)
-    right = np.zeros_like(L)
-    right[:, :, :-1] = Lq[:, :, 1:]
-    up = np.zeros_like(L)
-    up[:, 1:, :] = Lq[:, :-1, :]
-    want = L + a * right - b_ * up + c * gq + d * sq[:, None, None] + e + bias
-    np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+    dx = np.zeros_like(L)
+    dx[:, :, :-1] = q(16.0 * (L[:, :, 1:] - L[:, :, :-1]))
+    dy = np.zeros_like(L)
+    dy[:, :-1, :] = q(16.0 * (L[:, 1:, :] - L[:, :-1, :]))
+    gq, sq = q(g), q(np.log1p(tau) / 5.0)
+    right = np.zeros_like(L)          # dx at (y, x + 1)
+    right[:, :, :-1] = dx[:, :, 1:]
+    up = np.zeros_like(L)             # dy at (y - 1, x)
+    up[:, 1:, :] = dy[:, :-1, :]
+    z = a * right - b_ * up + c * gq + d * sq[:, None, None] + e + bias
+    np.testing.assert_allclose(got, L + z / 256.0, rtol=0, atol=1e-14)
+
+
+def test_constant_offset_leaves_the_step_unchanged():
+    # the inputs see L only through its differences, like the AOS step
+    r = _rng(9)
+    L = r.uniform(0, 0.5, (2, 7, 8))
+    g = r.uniform(0.1, 1, (2, 7, 8))
+    p = _random_params(10)
+    a, _ = so.forward(p, L, g, [1.0, 3.0], bf16=False)
+    b, _ = so.forward(p, L + 0.25, g, [1.0, 3.0], bf16=False)
+    np.testing.assert_allclose(b - 0.25, a, rtol=0, atol=1e-13)
 
 
 def _random_params(seed, scale=1.0):
