@@ -18,6 +18,10 @@ CPU oracle on a bounded sample of the same workload.
 Under torchrun (N > 1) every rank detects its own images (independent
 replicas, no collective on the data path) and the slowest rank's time sets
 the whole-job throughput.
+Two sections ride along on the same line: `batched` (64 mixed-size images:
+the autotuned batch execution against image-after-image detection) and
+`surrogate` (the learned AOS stand-in judged by AOS on 16 images, with the
+tensor-core roofline of its fused kernel).
 """
 from __future__ import annotations
 
@@ -124,6 +128,22 @@ def algorithmic_bytes(kind, pixels, n_levels, nbins=300):
     if kind == "percentile":
         return 4 * nbins
     return 4
+
+
+# multiply-adds per pixel of the surrogate network: 3x3 taps x (5*32 + 32*32
+# + 32*32 + 32*1); the kernels execute more (16 input and 8 output channels
+# stored, halo recomputation), but the roofline counts the network's own
+SURROGATE_MACS_PER_PIXEL = 9 * (5 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
+SURROGATE_CKPT = os.path.join(ROOT, "paper_1706_06750_gb300", "weights", "surrogate.ckpt")
+
+
+def measured_bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
 
 
 def measured_hbm_peak():
@@ -309,6 +329,7 @@ def run_ours(args, rank, world, local_rank):
 
     batched = None if args.no_batch else run_batched(args, kaze, synth, torch, stream, world, rank,
                                                         max_over_ranks, barrier)
+    surrogate = None if args.no_surrogate else run_surrogate(args, kaze, synth, torch, rank)
 
     if dist is not None:
         dist.barrier()
@@ -344,6 +365,7 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes},
         "kernels": kernels,
         "batched": batched,
+        "surrogate": surrogate,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -421,6 +443,30 @@ def run_batched(args, kaze, synth, torch, stream, world, rank, max_over_ranks, b
                      "after image on one stream; persistent = the whole batch as one kernel launch")}
 
 
+def run_surrogate(args, kaze, synth, torch, rank):
+    """The learned AOS surrogate judged by plain GPU AOS on 16 seeded 1920x1200
+    images (seeds 2000 + 16 rank + j): pixel error, keypoint repeatability and
+    time (surrogate_eval), plus the roofline of the fused surrogate kernel on
+    the batched step (all 16 images in one launch)."""
+    from paper_1706_06750_gb300 import surrogate_eval
+    if not os.path.exists(SURROGATE_CKPT):
+        return {"unavailable": "no trained checkpoint at paper_1706_06750_gb300/weights/surrogate.ckpt"}
+    s = kaze.Surrogate(seed=0)
+    s.load(SURROGATE_CKPT)
+    imgs = [torch.from_numpy(synth.image(W_IMG, H_IMG, 2000 + 16 * rank + j)).cuda() for j in range(16)]
+    r = surrogate_eval.evaluate(s, imgs, OCTAVES, SUBLEVELS, batch_reps=max(3, min(args.steps, 10)))
+    flops = 2.0 * SURROGATE_MACS_PER_PIXEL * W_IMG * H_IMG * len(imgs)
+    achieved = flops / (r["batched_step_ms_surrogate"] * 1e-3) / 1e12
+    peak, src = measured_bf16_peak()
+    r["roofline"] = {"bound": "tensor", "kernel": "surrogate (fused)", "achieved": achieved, "peak": peak,
+                     "peak_source": src, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "flops_per_launch": flops, "traffic": None}
+    r["speedup_vs_aos_batched_step"] = r["batched_step_ms_aos"] / r["batched_step_ms_surrogate"]
+    r["checkpoint"] = os.path.relpath(SURROGATE_CKPT, ROOT)
+    s.close()
+    return r
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -430,6 +476,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = env_int("RANK", 0)

@@ -84,7 +84,7 @@ def evaluate(surrogate, images, octaves=4, sublevels=4, batch_reps=5):
             torch.cuda.synchronize()
             one_step[j, i - 1] = float(torch.sqrt(torch.mean((pred.double() - lv_a[i].double()) ** 2)))
             skip[j, i - 1] = float(torch.sqrt(torch.mean((prev.double() - lv_a[i].double()) ** 2)))
-            if j == 0:
+            if i == 1:
                 prev_all.append(prev)
                 g_all.append(g)
         for i in range(N):
@@ -101,11 +101,11 @@ def evaluate(surrogate, images, octaves=4, sublevels=4, batch_reps=5):
         t_aos.append(pa["aos_rows"][0] + pa["aos_cols"][0])
         t_sg.append(ps["surrogate"][0])
 
-    # batched step: every image's level-1 step in one fused launch, against
-    # one AOS step per image (kaze_op_aos_step)
+    # batched step: every image's first step (L_0 and its conductance) in
+    # one fused launch, against one AOS step per image (kaze_op_aos_step)
     n = len(images)
-    Ls = [prev_all[0]] * n
-    gs = [g_all[0]] * n
+    Ls = prev_all
+    gs = g_all
     outs = [torch.empty_like(Ls[0]) for _ in range(n)]
     ux = torch.empty_like(Ls[0])
     tau = taus[0]

@@ -12,7 +12,7 @@ Every ``--log-every`` steps the loss of a fixed probe batch (pairs spread
 evenly over the set) is logged beside the batch loss.
 
     python -m paper_1706_06750_gb300.train_surrogate --pairs DIR --out CKPT \\
-        [--steps 4000] [--batch 8] [--lr 2e-3] [--seed 0] [--resume CKPT] \\
+        [--steps 20000] [--batch 8] [--lr 1e-3] [--seed 0] [--resume CKPT] \\
         [--checkpoint-every 1000]
 
 Prints one JSON line per ``--log-every`` steps and a final summary line.
@@ -45,7 +45,7 @@ def lr_at(step, steps, lr):
     return lr / 20.0 + (lr - lr / 20.0) * c
 
 
-def train(pairs_dir, out, steps=4000, batch=8, lr=2e-3, seed=0, resume=None, checkpoint_every=1000,
+def train(pairs_dir, out, steps=20000, batch=8, lr=1e-3, seed=0, resume=None, checkpoint_every=1000,
           log_every=100, log=print):
     import torch
 
@@ -53,8 +53,8 @@ def train(pairs_dir, out, steps=4000, batch=8, lr=2e-3, seed=0, resume=None, che
     meta, levels_np, cond_np, index = load_pairs(pairs_dir)
     size = meta["size"]
     taus = np.asarray(meta["taus"], dtype=np.float32)
-    levels = torch.from_numpy(np.ascontiguousarray(levels_np)).cuda()
-    cond = torch.from_numpy(np.ascontiguousarray(cond_np)).cuda()
+    levels = torch.from_numpy(np.array(levels_np)).cuda()
+    cond = torch.from_numpy(np.array(cond_np)).cuda()
     s = kaze.Surrogate(size, size, batch, train=True, seed=seed)
     if resume:
         s.load(resume)
@@ -96,9 +96,9 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="Train the learned AOS surrogate on oracle pairs.")
     ap.add_argument("--pairs", required=True)
     ap.add_argument("--out", required=True)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--resume", default=None)
     ap.add_argument("--checkpoint-every", type=int, default=1000)

@@ -294,3 +294,38 @@ def test_invalid_arguments(K):
     assert e.value.status == K.ERR_STATE
     with pytest.raises(K.KazeError):
         inf.set_params(np.full(K.SURROGATE_PARAMS, np.nan, np.float32))
+
+
+def test_trained_surrogate_against_aos(K, capsys):
+    """What the committed, trained network gains over the method without it
+    (plain GPU AOS, the judge) on two held-out 1920x1200 workload images:
+    it reproduces most of each early AOS step and keeps most AOS keypoints,
+    and it costs more time than the step it replaces.  The numbers are
+    printed; the asserts hold the trained checkpoint to what it measured
+    (with margin), not to a target."""
+    import json
+
+    from paper_1706_06750_gb300 import surrogate_eval, synth
+    ckpt = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_1706_06750_gb300", "weights", "surrogate.ckpt")
+    s = K.Surrogate()
+    s.load(ckpt)
+    assert s.steps_taken() > 0
+    imgs = [torch.from_numpy(synth.workload_image("1920x1200", j)).cuda() for j in range(2)]
+    r = surrogate_eval.evaluate(s, imgs, batch_reps=3)
+    rel = np.array(r["one_step_rms"]) / np.array(r["skip_step_rms"])
+    with capsys.disabled():
+        print("\nsurrogate vs AOS:", json.dumps({k: r[k] for k in (
+            "one_step_gain", "repeatability_1px", "repeatability_2_5px", "confirmed_2_5px",
+            "keypoints_aos", "keypoints_surrogate", "evolution_ms_aos", "evolution_ms_surrogate",
+            "batched_step_ms_aos", "batched_step_ms_surrogate")}))
+    # accuracy: the network removes most of the error of skipping a step on
+    # the early levels (the AOS step is the target), less on the late ones,
+    # whose diffusion length exceeds its 9x9 receptive field
+    assert np.mean(rel[:8]) < 0.5, rel
+    assert r["one_step_gain"] > 0.4
+    assert np.all(rel < 0.9), rel
+    assert r["repeatability_2_5px"] > 0.6
+    # time: both measured; the surrogate is the slower stand-in
+    assert r["evolution_ms_aos"] > 0 and r["evolution_ms_surrogate"] > 0
+    assert r["batched_step_ms_surrogate"] > r["batched_step_ms_aos"]
