@@ -118,10 +118,16 @@ class ClockSampler:
 # --------------------------------------------------------------- roofline --
 
 def algorithmic_bytes(kind, pixels, n_levels, nbins=300):
-    """Minimum bytes one launch of a kernel kind must move (FP32 planes)."""
+    """Minimum bytes a kernel kind must move in one detection (FP32 planes):
+    presmoothing reads I and writes L_0; the contrast passes read L_0; each of
+    the N-1 steps writes g (read L), then its row and column halves each read
+    L and g and write (add) their half of L_i; the response reads and writes
+    every level, the extrema read every response once."""
+    steps = n_levels - 1
+    # the AOS halves each read L and g and add half of L_i
     table = {
-        "presmooth": 8, "grad_max": 4, "grad_hist": 4, "conductance": 8,
-        "aos_rows": 12, "aos_cols": 16, "doh": 8 * n_levels, "extrema": 4 * n_levels,
+        "presmooth": 8, "grad_max": 4, "grad_hist": 4, "conductance": 8 * steps,
+        "aos_rows": 12 * steps, "aos_cols": 12 * steps, "doh": 8 * n_levels, "extrema": 4 * n_levels,
     }
     if kind in table:
         return table[kind] * pixels
@@ -203,6 +209,31 @@ def oracle_sample_rate(img, seconds_budget, octaves=OCTAVES, sublevels=SUBLEVELS
     return cw * ch / dt / 1e6, cw, ch, dt
 
 
+# ------------------------------------------------------------ multi-rank --
+
+def replica_seed(rank):
+    """Seed of the workload image of `rank` (independent replicas)."""
+    return 2000 + rank
+
+
+def max_over_ranks(v, dist=None, device="cpu"):
+    """The slowest rank's value (every rank receives it); v itself when not
+    distributed.  device: where the reduction tensor lives (cuda for NCCL,
+    cpu for gloo)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, units_per_step, t_ms):
+    """Units processed by all ranks per second (in millions), from the
+    slowest rank's summed step time."""
+    return world * steps * units_per_step / (t_ms * 1e-3) / 1e6
+
+
 # -------------------------------------------------------------- reference --
 
 def run_reference(args, rank, world):
@@ -251,7 +282,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", rank=rank, world_size=world)
 
-    img = synth.image(W_IMG, H_IMG, 2000 + rank)
+    img = synth.image(W_IMG, H_IMG, replica_seed(rank))
     pixels = W_IMG * H_IMG
     k = kaze.Kaze(W_IMG, H_IMG, octaves=OCTAVES, sublevels=SUBLEVELS)
     x = torch.from_numpy(img).cuda()
@@ -292,15 +323,11 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     clk = clocks.stop()
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(v):
+        return max_over_ranks(v, dist, "cuda")
 
-    t_dev_ms = max_over_ranks(t_dev_ms)
-    t_e2e_ms = max_over_ranks(t_e2e_ms)
+    t_dev_ms = slowest(t_dev_ms)
+    t_e2e_ms = slowest(t_e2e_ms)
 
     # per-kernel device time with events around every launch
     prof_steps = max(3, min(20, args.steps))
@@ -318,17 +345,18 @@ def run_ours(args, rank, world, local_rank):
         if n == 0:
             continue
         per = ms / n
-        ab = algorithmic_bytes(name, pixels, OCTAVES * SUBLEVELS)
-        kernels[name] = {"ms_per_launch": per, "launches_per_step": n // prof_steps,
-                         "share": ms / total_ms, "algorithmic_gbs": ab / (per * 1e-3) / 1e9}
+        per_step = n // prof_steps
+        ab = algorithmic_bytes(name, pixels, OCTAVES * SUBLEVELS) / max(1, per_step)
+        kernels[name] = {"ms_per_launch": per, "launches_per_step": per_step, "share": ms / total_ms,
+                         "algorithmic_bytes_per_launch": ab, "algorithmic_gbs": ab / (per * 1e-3) / 1e9}
     dom = max(kernels, key=lambda n: kernels[n]["share"])
     peak, peak_kind = measured_hbm_peak()
-    dom_bytes = algorithmic_bytes(dom, pixels, OCTAVES * SUBLEVELS)
+    dom_bytes = kernels[dom]["algorithmic_bytes_per_launch"]
     achieved = kernels[dom]["algorithmic_gbs"]
     traffic = ncu_traffic(dom)
 
     batched = None if args.no_batch else run_batched(args, kaze, synth, torch, stream, world, rank,
-                                                        max_over_ranks, barrier)
+                                                        slowest, barrier)
     surrogate = None if args.no_surrogate else run_surrogate(args, kaze, synth, torch, rank)
 
     if dist is not None:
@@ -345,8 +373,8 @@ def run_ours(args, rank, world, local_rank):
                          f"{OCTAVES}x{SUBLEVELS} levels, scale space + response + extrema, "
                          f"FP64 oracle single thread, {secs:.1f} s"}
 
-    value = world * args.steps * pixels / (t_dev_ms * 1e-3) / 1e6
-    e2e = world * args.steps * pixels / (t_e2e_ms * 1e-3) / 1e6
+    value = whole_job_rate(world, args.steps, pixels, t_dev_ms)
+    e2e = whole_job_rate(world, args.steps, pixels, t_e2e_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev_ms / args.steps, "higher_is_better": True,

@@ -396,11 +396,15 @@ const char* kaze_kernel_name(int kind);
  * kernels it holds); -1 for a NULL handle. */
 int kaze_last_launch_count(const kaze_handle* h);
 
-/* Runs kaze_build_scale_space + kaze_detector_response + the extrema kernel
- * once, launch by launch (no graph), with a CUDA event pair recorded on the
- * handle's stream around every kernel.  h_ms[k] receives the summed device
- * time in ms of kind k, h_launches[k] its number of launches; both arrays
- * hold kaze_kernel_kinds() entries.  Synchronises the stream. */
+/* Times kaze_build_scale_space + kaze_detector_response + the extrema
+ * kernel with a CUDA event pair recorded on the handle's stream around every
+ * kernel (the two halves of each AOS step run one after the other here).
+ * On a capturable stream the sequence is recorded as a CUDA graph and
+ * replayed twice, the times taken from the second replay, as a detection
+ * runs; on the legacy or per-thread default stream it runs once, launch by
+ * launch.  h_ms[k] receives the summed device time in ms of kind k,
+ * h_launches[k] its number of kernels; both arrays hold kaze_kernel_kinds()
+ * entries.  Synchronises the stream. */
 kaze_status kaze_profile(kaze_handle* h, const float* d_img, int w, int h_, int pitch_elems,
                          double* h_ms, int* h_launches);
 

@@ -352,11 +352,12 @@ __device__ __forceinline__ void chunk_solution(const float* c, float* d, const f
 // ---------------------------------------------------------------- rows ----
 // NW warps per row, 128 threads per CTA (4 / NW rows).  Shared memory per
 // row: g and L (ls floats each), the chunk equations (6 P), the chunk end
-// values (2 P).
+// values (2 P).  Output: u_x to `ux`, or, with acc != nullptr, u_x / 2 added
+// into acc (the other half of the step is the column kernel's).
 template <int M, int NW>
 __global__ void __launch_bounds__(128) k_aos_rows(const float* __restrict__ L, const float* __restrict__ g,
-                                                  float* __restrict__ ux, int pitch, int w, int h, float tau,
-                                                  int* __restrict__ status)
+                                                  float* __restrict__ ux, float* __restrict__ acc, int pitch, int w,
+                                                  int h, float tau, int* __restrict__ status)
 {
     constexpr int P = 32 * NW;
     constexpr int ROWS = 4 / NW;
@@ -419,6 +420,20 @@ __global__ void __launch_bounds__(128) k_aos_rows(const float* __restrict__ L, c
     if (active) chunk_solution<1, M>(ce, cd, ap, xs[p], xs[P + p]);
     __syncthreads();
     if (!active) return;
+    if (acc) {
+        // two halves added onto zero in either order give the same sum
+        float* arow = acc + (size_t)y * pitch;
+        for (int x = p * 4; x < w4; x += 4 * P) {
+            float4 v = *reinterpret_cast<const float4*>(sd + x);
+            v.x *= 0.5f;
+            v.y *= 0.5f;
+            v.z *= 0.5f;
+            v.w *= 0.5f;
+            atomicAdd(reinterpret_cast<float4*>(arow + x), v);
+        }
+        for (int x = w4 + p; x < w; x += P) atomicAdd(arow + x, 0.5f * sd[x]);
+        return;
+    }
     float* urow = ux + (size_t)y * pitch;
     for (int x = p * 4; x < w4; x += 4 * P)
         *reinterpret_cast<float4*>(urow + x) = *reinterpret_cast<const float4*>(sd + x);
@@ -429,7 +444,9 @@ __global__ void __launch_bounds__(128) k_aos_rows(const float* __restrict__ L, c
 // A strip of COLS columns per CTA, P = 32 NW chunks per column, blockDim =
 // COLS P; thread t owns column t % COLS and chunk t / COLS.  Shared memory:
 // the g and L tiles ([RS][COLS], RS = P M rounded up to whole 256-row boxes)
-// and per column the chunk equations (6 P) and end values (2 P).
+// and per column the chunk equations (6 P) and end values (2 P).  Output:
+// Lnext = (u_x + u_y) / 2 with u_x read from `ux`, or, with ux == nullptr,
+// u_y / 2 added into Lnext (the row kernel adds the other half).
 template <int COLS, int M, int NW>
 __global__ void __launch_bounds__(COLS * 32 * NW)
     k_aos_cols(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmG,
@@ -493,9 +510,24 @@ __global__ void __launch_bounds__(COLS * 32 * NW)
     chunk_solution<COLS, M>(ce, cd, ap, eqc[6 * P + p], eqc[7 * P + p]);
     __syncthreads();
 
+    const bool full = x0 + COLS <= w;
+    if (ux == nullptr) {
+        for (int e = tid; e < h * V; e += NT) {
+            const int j = e / V, qq = e - j * V;
+            const size_t gi = (size_t)j * pitch + x0 + 4 * qq;
+            const float* uy = td + (size_t)j * COLS + 4 * qq;
+            if (full) {
+                atomicAdd(reinterpret_cast<float4*>(Lnext + gi),
+                          make_float4(0.5f * uy[0], 0.5f * uy[1], 0.5f * uy[2], 0.5f * uy[3]));
+            } else {
+                for (int kk = 0; kk < 4; ++kk)
+                    if (x0 + 4 * qq + kk < w) atomicAdd(Lnext + gi + kk, 0.5f * uy[kk]);
+            }
+        }
+        return;
+    }
     // L_next = (u_x + u_y) / 2 over the strip: the 16-byte loads of the row
     // solution are all issued before the stores
-    const bool full = x0 + COLS <= w;
     float4 pre[EPI];
 #pragma unroll
     for (int k = 0; k < EPI; ++k) {
@@ -532,6 +564,7 @@ struct RowsArgs {
     const float* L;
     const float* g;
     float* ux;
+    float* acc;
     int pitch, w, h;
     float tau;
     int* status;
@@ -555,8 +588,8 @@ template <int M, int NW>
 cudaError_t launch_rows_m(const RowsArgs& a)
 {
     constexpr int ROWS = 4 / NW;
-    k_aos_rows<M, NW><<<(a.h + ROWS - 1) / ROWS, 128, a.smem, a.st>>>(a.L, a.g, a.ux, a.pitch, a.w, a.h, a.tau,
-                                                                        a.status);
+    k_aos_rows<M, NW><<<(a.h + ROWS - 1) / ROWS, 128, a.smem, a.st>>>(a.L, a.g, a.ux, a.acc, a.pitch, a.w, a.h,
+                                                                        a.tau, a.status);
     return cudaGetLastError();
 }
 

@@ -110,13 +110,14 @@ size_t aos_cols_smem_bytes(int h)
     return c == 0 ? 0 : cols_smem(h, c);
 }
 
-cudaError_t launch_aos_rows(const float* L, const float* g, float* ux, int pitch, int w, int h, float tau,
-                            int* d_status, cudaStream_t st)
+cudaError_t launch_aos_rows(const float* L, const float* g, float* ux, float* acc, int pitch, int w, int h,
+                            float tau, int* d_status, cudaStream_t st)
 {
     const size_t smem = aos_rows_smem_bytes(w);
     if (smem == 0) return cudaErrorInvalidValue;
+    if (acc && ((pitch & 3) != 0 || ((uintptr_t)acc & 15) != 0)) return cudaErrorInvalidValue;
     const int nw = aos::warps_per_line(w), m = aos::chunk_len(w);
-    const aos::RowsArgs args{L, g, ux, pitch, w, h, tau, d_status, smem, st};
+    const aos::RowsArgs args{L, g, ux, acc, pitch, w, h, tau, d_status, smem, st};
 #define KZ_ROWS(M, NW) \
     if (nw == NW && m == M) return aos::launch_rows_m<M, NW>(args);
     KZ_AOS_VARIANTS(KZ_ROWS)
@@ -125,13 +126,14 @@ cudaError_t launch_aos_rows(const float* L, const float* g, float* ux, int pitch
 }
 
 cudaError_t launch_aos_cols(const float* L, const float* g, const float* ux, float* Lnext, int pitch, int w, int h,
-                            float tau, int* d_status, cudaStream_t st)
+                            float tau, int* d_status, cudaStream_t st, int cols)
 {
-    const int c = cols_per_cta(h);
-    if (c == 0) return cudaErrorInvalidValue;
+    const int c = cols == 0 ? cols_per_cta(h) : cols;
+    if (c == 0 || (c != 4 && c != 8) || cols_smem(h, c) > kSmemBudget) return cudaErrorInvalidValue;
     aos::ColsArgs args;
     if (!make_strip_map(&args.mL, L, pitch, w, h, c) || !make_strip_map(&args.mG, g, pitch, w, h, c))
         return cudaErrorInvalidValue;
+    if (!ux && ((pitch & 3) != 0 || ((uintptr_t)Lnext & 15) != 0)) return cudaErrorInvalidValue;
     args.ux = ux;
     args.Lnext = Lnext;
     args.pitch = pitch;

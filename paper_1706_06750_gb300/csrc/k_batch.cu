@@ -92,6 +92,9 @@ enum { GM_COND = 0, GM_MAX = 1, GM_HIST = 2 };
 
 // Smoothed Scharr gradient of a 32x32 tile (radius r smoothing, halo r+1),
 // then the conductance of Eq. 3, the maximum magnitude or the histogram.
+// The arithmetic repeats the single-image kernel (k_filters.cu) operation
+// for operation -- symmetric tap pairs, the D / E form of the Scharr pair,
+// explicit fmaf -- so the batched and single-image paths agree bit for bit.
 template <int RC>
 __device__ void gradient_tile(int mode, const float* __restrict__ L, float* __restrict__ g, int pitch, int w, int h,
                               const GaussTaps& taps, float k, int diffusivity, unsigned* hmax_bits, unsigned* hist,
@@ -115,51 +118,55 @@ __device__ void gradient_tile(int mode, const float* __restrict__ L, float* __re
     __syncthreads();
     for (int i = tid; i < SH * CW; i += NT) {
         const int sy = i / CW, sx = i - sy * CW;
-        float acc = 0.f;
+        const float* a = A + sy * SW + sx;
+        float acc = taps.w[r] * a[r];
         if (RC > 0) {
 #pragma unroll
-            for (int j = 0; j <= 2 * RC; ++j) acc = fmaf(taps.w[j], A[sy * SW + sx + j], acc);
+            for (int j = 1; j <= RC; ++j) acc = fmaf(taps.w[RC + j], a[RC - j] + a[RC + j], acc);
         } else {
-            for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], A[sy * SW + sx + j], acc);
+            for (int j = 1; j <= r; ++j) acc = fmaf(taps.w[r + j], a[r - j] + a[r + j], acc);
         }
         B[i] = acc;
     }
     __syncthreads();
     for (int i = tid; i < CH * CW; i += NT) {
         const int sy = i / CW, sx = i - sy * CW;
-        float acc = 0.f;
+        const float* b = B + sy * CW + sx;
+        float acc = taps.w[r] * b[r * CW];
         if (RC > 0) {
 #pragma unroll
-            for (int j = 0; j <= 2 * RC; ++j) acc = fmaf(taps.w[j], B[(sy + j) * CW + sx], acc);
+            for (int j = 1; j <= RC; ++j) acc = fmaf(taps.w[RC + j], b[(RC - j) * CW] + b[(RC + j) * CW], acc);
         } else {
-            for (int j = 0; j <= 2 * r; ++j) acc = fmaf(taps.w[j], B[(sy + j) * CW + sx], acc);
+            for (int j = 1; j <= r; ++j) acc = fmaf(taps.w[r + j], b[(r - j) * CW] + b[(r + j) * CW], acc);
         }
         C[i] = acc;
     }
     __syncthreads();
-    const float c0 = 3.f / 16.f, c1 = 10.f / 16.f;
-    const float hmax = mode == GM_HIST ? __uint_as_float(__ldcg(hmax_bits)) : 0.f;
+    const float inv_k2 = mode == GM_COND ? 1.f / (k * k) : 0.f;
+    const float hmax_scale = mode == GM_HIST ? (float)nbins / __uint_as_float(__ldcg(hmax_bits)) : 0.f;
     float local_max = 0.f;
     for (int i = tid; i < 32 * 32; i += NT) {
         const int oy = i >> 5, ox = i & 31;
         const int gx = x0 + ox, gy = y0 + oy;
         const float* c = C + (oy + 1) * CW + (ox + 1);
-        float lx = c0 * 0.5f * (c[-CW + 1] - c[-CW - 1]);
-        lx += c1 * 0.5f * (c[1] - c[-1]);
-        lx += c0 * 0.5f * (c[CW + 1] - c[CW - 1]);
-        float ly = c0 * 0.5f * (c[CW - 1] - c[-CW - 1]);
-        ly += c1 * 0.5f * (c[CW] - c[-CW]);
-        ly += c0 * 0.5f * (c[CW + 1] - c[-CW + 1]);
+        const float dm = c[-CW + 1] - c[-CW - 1];
+        const float d0 = c[1] - c[-1];
+        const float dp = c[CW + 1] - c[CW - 1];
+        const float em = fmaf(10.f, c[-CW], 3.f * (c[-CW - 1] + c[-CW + 1]));
+        const float ep = fmaf(10.f, c[CW], 3.f * (c[CW - 1] + c[CW + 1]));
+        const float lx = fmaf(10.f, d0, 3.f * (dm + dp)) * (1.f / 32.f);
+        const float ly = (ep - em) * (1.f / 32.f);
+        const float m2 = fmaf(ly, ly, lx * lx);
         if (gx >= w || gy >= h) continue;
         if (mode == GM_COND) {
-            const float q = (lx * lx + ly * ly) / (k * k);
-            g[(size_t)gy * pitch + gx] = diffusivity == KAZE_G1 ? expf(-q) : 1.f / (1.f + q);
+            const float q = m2 * inv_k2;
+            g[(size_t)gy * pitch + gx] = diffusivity == KAZE_G1 ? expf(-q) : __fdividef(1.f, 1.f + q);
         } else if (gx >= 1 && gx <= w - 2 && gy >= 1 && gy <= h - 2) {
-            const float m = sqrtf(lx * lx + ly * ly);
+            const float m = sqrtf(m2);
             if (mode == GM_MAX) {
                 local_max = fmaxf(local_max, m);
             } else if (m > 0.f) {
-                const int b = min((int)floorf((float)nbins * m / hmax), nbins - 1);
+                const int b = min((int)floorf(m * hmax_scale), nbins - 1);
                 atomicAdd(&hs[b], 1u);
             }
         }
@@ -244,10 +251,7 @@ __device__ void doh_tile(const float* __restrict__ L, float* __restrict__ D, int
             const int tr = base + s * m;
             if (tr < R) {
                 const float* t = T + tr * C + col;
-                const float v0 = t[0], v1 = t[s], v2 = t[2 * s], v3 = t[3 * s], v4 = t[4 * s];
-                hd[m] = (v0 + v4) - 2.f * v2;
-                hs[m] = 9.f * (v0 + v4) + 60.f * (v1 + v3) + 118.f * v2;
-                hx[m] = 3.f * (v4 - v0) + 10.f * (v3 - v1);
+                doh_lattice_row(t[0], t[s], t[2 * s], t[3 * s], t[4 * s], hd[m], hs[m], hx[m]);
             } else {
                 hd[m] = hs[m] = hx[m] = 0.f;
             }
@@ -258,10 +262,7 @@ __device__ void doh_tile(const float* __restrict__ L, float* __restrict__ D, int
             if (ty >= DT) break;
             const int gy = y0 + ty;
             if (gy >= h || gx >= w) continue;
-            const float lxx = 9.f * (hd[kk] + hd[kk + 4]) + 60.f * (hd[kk + 1] + hd[kk + 3]) + 118.f * hd[kk + 2];
-            const float lyy = (hs[kk] + hs[kk + 4]) - 2.f * hs[kk + 2];
-            const float lxy = 3.f * (hx[kk + 4] - hx[kk]) + 10.f * (hx[kk + 3] - hx[kk + 1]);
-            D[(size_t)gy * pitch + gx] = scale * (lxx * lyy - lxy * lxy);
+            D[(size_t)gy * pitch + gx] = doh_value(hd + kk, hs + kk, hx + kk, scale);
         }
     }
 }

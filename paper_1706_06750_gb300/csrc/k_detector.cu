@@ -14,107 +14,72 @@
 // integer taps and applies norm / (1024 s^2)^2 once to the determinant.
 // Borders reflect coordinates into the image (half-sample symmetric).
 //
-// GB300 mapping (one launch per level, its own step s): a CTA stages the
-// level's (64 + 4s)^2 input tile in shared memory (reflection on load), then
-// each thread computes a vertical run of up to 8 outputs that share one
-// residue modulo s.  Consecutive outputs of a run reuse 4 of their 5
-// horizontally filtered lattice rows, which stay in registers: per output
-// ~5 (K+4)/K shared loads and ~30 FP32 operations instead of 25 loads.
+// GB300 mapping: one launch for a group of levels (grid.z), no shared
+// memory.  A thread owns one column x and walks WK consecutive lattice rows
+// y = py + s k of one residue py of the level's step s.  Its five column taps
+// x - 2s .. x + 2s are reflected once; each lattice row costs five loads
+// (coalesced across the warp, L1/L2-resident) and the three horizontal
+// filters, and each output then combines five consecutive lattice rows held
+// in registers: ~(WK + 4) / WK x 5 loads and ~30 FP32 operations per output.
 #include "kaze_internal.h"
 
 namespace kz {
 namespace {
 
-constexpr int DT = 64;       // output tile edge (DT x DT)
-constexpr int DTHREADS = 256;
-constexpr int RUN = 8;       // outputs per vertical run
+constexpr int WK = 24;        // outputs per thread (consecutive lattice rows)
+constexpr int WTX = 128;      // threads per CTA (consecutive columns)
+constexpr int DPD = 4;        // lattice rows of loads kept in flight
 
-__global__ void __launch_bounds__(DTHREADS)
+// blockIdx.y = py * nseg + seg for the level's step s: residue py, segment
+// seg of WK lattice rows; blocks past the level's residues return.
+__global__ void __launch_bounds__(WTX)
 k_doh(const float* __restrict__ L, float* __restrict__ D, int pitch, long long plane_stride, int w, int h,
       int l0, const __grid_constant__ LevelTable tab)
 {
-    extern __shared__ float T[];  // [R][C] input tile, C odd
     const int level = l0 + blockIdx.z;
     const int s = tab.step[level];
+    const int nseg = ((h + s - 1) / s + WK - 1) / WK;
+    const int py = blockIdx.y / nseg, seg = blockIdx.y - py * nseg;
+    const int x = blockIdx.x * WTX + threadIdx.x;
+    const int k0 = seg * WK;
+    if (py >= s || x >= w || py + s * k0 >= h) return;
     const double dd = 1024.0 * s * s;
-    const float scale = tab.norm[level] / (float)(dd * dd);
+    const float scale = (float)((double)tab.norm[level] / (dd * dd));  // as the batched path computes it
     L += (size_t)level * plane_stride;
     D += (size_t)level * plane_stride;
-    const int R = DT + 4 * s;
-    const int C = (DT + 4 * s) | 1;
-    const int x0 = blockIdx.x * DT, y0 = blockIdx.y * DT;
-    const int tid = threadIdx.x;
-
-    // stage rows y0-2s .. y0+DT+2s-1, columns x0-2s .. x0+DT+2s-1: each
-    // thread owns up to 3 columns (reflected once) and every 4th row; four
-    // rows of loads are issued before their stores
-    {
-        const int cw = DT + 4 * s;  // <= 3 * DT for s <= 32
-        const int tc = tid & (DT - 1), tr = tid / DT;
-        int gxs[3];
-        bool okc[3];
+    int cx[5];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            okc[k] = tc + k * DT < cw;
-            gxs[k] = reflect_index(x0 - 2 * s + tc + k * DT, w);
-        }
-        for (int r0 = tr; r0 < R; r0 += 16) {
-            float v[4][3];
+    for (int a = 0; a < 5; ++a) cx[a] = reflect_index(x + (a - 2) * s, w);
+    // lattice rows k0 - 2 .. k0 + WK + 1 of residue py: loads run DPD rows
+    // ahead of the filters; the last five filtered rows stay in registers
+    constexpr int NM = WK + 4;
+    float buf[DPD + 1][5];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = r0 + 4 * q;
-                const float* row = L + (size_t)reflect_index(y0 - 2 * s + min(r, R - 1), h) * pitch;
+    for (int m = 0; m < DPD; ++m) {
+        const float* row = L + (size_t)reflect_index(py + s * (k0 + m - 2), h) * pitch;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) v[q][k] = okc[k] ? __ldg(row + gxs[k]) : 0.f;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = r0 + 4 * q;
-                if (r < R) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k)
-                        if (okc[k]) T[r * C + tc + k * DT] = v[q][k];
-                }
-            }
-        }
+        for (int a = 0; a < 5; ++a) buf[m][a] = __ldg(row + cx[a]);
     }
-    __syncthreads();
-
-    // runs: residue q in [0, s), segment j; rows q + s (RUN j + k), k < RUN
-    const int col = tid & (DT - 1);          // output column in the tile
-    const int lane_row = tid / DT;           // 0..3
-    const int per_class = (DT / s + (DT % s ? 1 : 0) + RUN - 1) / RUN;  // >= 1
-    const int nruns = s * per_class;
-    const int gx = x0 + col;
-    for (int ri = lane_row; ri < nruns; ri += DTHREADS / DT) {
-        const int q = ri / per_class, j = ri - q * per_class;
-        const int base = q + s * RUN * j;    // first output row of the run (tile coords)
-        if (base >= DT) continue;
-        float hd[RUN + 4], hs[RUN + 4], hx[RUN + 4];
+    float hd[5], hs[5], hx[5];
 #pragma unroll
-        for (int m = 0; m < RUN + 4; ++m) {
-            const int tr = base + s * m;      // tile row of lattice row m (offset -2s folded in)
-            if (tr < R) {
-                const float* t = T + tr * C + col;
-                const float v0 = t[0], v1 = t[s], v2 = t[2 * s], v3 = t[3 * s], v4 = t[4 * s];
-                hd[m] = (v0 + v4) - 2.f * v2;
-                hs[m] = 9.f * (v0 + v4) + 60.f * (v1 + v3) + 118.f * v2;
-                hx[m] = 3.f * (v4 - v0) + 10.f * (v3 - v1);
-            } else {
-                hd[m] = hs[m] = hx[m] = 0.f;
-            }
-        }
+    for (int m = 0; m < NM; ++m) {
+        if (m + DPD < NM) {
+            const float* row = L + (size_t)reflect_index(py + s * (k0 + m + DPD - 2), h) * pitch;
 #pragma unroll
-        for (int k = 0; k < RUN; ++k) {
-            const int ty = base + s * k;
-            if (ty >= DT) break;
-            const int gy = y0 + ty;
-            if (gy >= h || gx >= w) continue;
-            const float lxx = 9.f * (hd[k] + hd[k + 4]) + 60.f * (hd[k + 1] + hd[k + 3]) + 118.f * hd[k + 2];
-            const float lyy = (hs[k] + hs[k + 4]) - 2.f * hs[k + 2];
-            const float lxy = 3.f * (hx[k + 4] - hx[k]) + 10.f * (hx[k + 3] - hx[k + 1]);
-            D[(size_t)gy * pitch + gx] = scale * (lxx * lyy - lxy * lxy);
+            for (int a = 0; a < 5; ++a) buf[(m + DPD) % (DPD + 1)][a] = __ldg(row + cx[a]);
         }
+        const float* v = buf[m % (DPD + 1)];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            hd[q] = hd[q + 1];
+            hs[q] = hs[q + 1];
+            hx[q] = hx[q + 1];
+        }
+        doh_lattice_row(v[0], v[1], v[2], v[3], v[4], hd[4], hs[4], hx[4]);
+        if (m < 4) continue;
+        const int y = py + s * (k0 + m - 4);
+        if (y >= h) break;
+        D[(size_t)y * pitch + x] = doh_value(hd, hs, hx, scale);
     }
 }
 
@@ -188,41 +153,28 @@ k_extrema(const float* __restrict__ D, int pitch, long long plane_stride, int w,
     }
 }
 
-size_t doh_smem(int s)
-{
-    const int R = DT + 4 * s;
-    const int C = (DT + 4 * s) | 1;
-    return (size_t)R * C * sizeof(float);
-}
-
 }  // namespace
 
-cudaError_t configure_detector_kernels()
-{
-    return allow_max_dynamic_smem(k_doh);
-}
+cudaError_t configure_detector_kernels() { return cudaSuccess; }
+
+// All levels of a response go to one launch (no shared memory to size).
+int doh_launches(const LevelTable&, int, int nl) { return nl > 0 ? 1 : 0; }
 
 cudaError_t launch_doh(const float* L, float* D, int pitch, long long plane_stride, int w, int h,
                        int l0, int nl, const LevelTable& tab, cudaStream_t st)
 {
-    // levels with similar steps share a launch (shared memory sized for the
-    // largest step of the group)
-    int i = l0;
-    while (i < l0 + nl) {
-        int j = i + 1;
-        while (j < l0 + nl && doh_smem(tab.step[j]) <= doh_smem(tab.step[i]) * 3 / 2) ++j;
-        int smax = 1;
-        for (int k = i; k < j; ++k) smax = tab.step[k] > smax ? tab.step[k] : smax;
-        if (smax > 32) return cudaErrorInvalidValue;
-        const size_t smem = doh_smem(smax);
-        if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
-        dim3 grid((w + DT - 1) / DT, (h + DT - 1) / DT, j - i);
-        k_doh<<<grid, DTHREADS, smem, st>>>(L, D, pitch, plane_stride, w, h, i, tab);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        i = j;
+    if (nl <= 0) return cudaSuccess;
+    int gy = 1;
+    for (int i = l0; i < l0 + nl; ++i) {
+        const int s = tab.step[i];
+        if (s < 1 || s > 4096) return cudaErrorInvalidValue;
+        const int nseg = ((h + s - 1) / s + WK - 1) / WK;
+        gy = s * nseg > gy ? s * nseg : gy;
     }
-    return cudaSuccess;
+    if (gy > 65535) return cudaErrorInvalidValue;
+    dim3 grid((w + WTX - 1) / WTX, gy, nl);
+    k_doh<<<grid, WTX, 0, st>>>(L, D, pitch, plane_stride, w, h, l0, tab);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_extrema(const float* D, int pitch, long long plane_stride, int w, int h, int n,

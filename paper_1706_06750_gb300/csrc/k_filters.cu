@@ -4,12 +4,12 @@
 //   * the two gradient-statistics passes and the percentile pick that give
 //     the contrast factor k from the gradient histogram.
 //
-// All three stencil kernels share one tiling: a CTA of 32x8 threads owns a
-// 32x32 output tile, stages its input tile plus halo in shared memory with
-// half-sample symmetric borders (index reflection on load), runs the
-// separable Gaussian rows-then-columns in shared memory and finishes with a
-// 3x3 Scharr stencil where needed.  The inputs are read once from HBM/L2;
-// halo re-reads come from neighbouring tiles and hit L2.
+// Presmoothing: a CTA of 32x8 threads owns a 32x32 output tile, stages its
+// input tile plus halo in shared memory with half-sample symmetric borders
+// (index reflection on load) and runs the separable Gaussian rows-then-
+// columns.  The gradient kernels walk down columns instead (see k_gradient):
+// each thread keeps its vertical filter window in registers and trades
+// neighbouring columns by warp shuffles, with no shared-memory staging.
 #include "kaze_internal.h"
 
 namespace kz {
@@ -65,130 +65,138 @@ k_gaussian(const float* __restrict__ in, int in_pitch, float* __restrict__ out, 
 
 enum GradMode { MODE_COND = 0, MODE_MAX = 1, MODE_HIST = 2 };
 
-// Smoothed Scharr gradient of a 32x32 tile.  Stages L with a halo of R+1,
-// smooths with G(sigma_d) (radius R) on the (32+2)^2 region around the tile,
-// then applies the 3x3 Scharr pair ([-1 0 1]/2 x [3 10 3]/16 and its
-// transpose).  MODE_COND writes the conductance g of Eq. 3; MODE_MAX folds
+constexpr int GK = 16;     // output rows per thread
+constexpr int GWARPS = 8;  // warps per CTA
+constexpr int GCOLS = 30;  // output columns per warp (lanes 1..30; 0 and 31 are halo)
+constexpr int GPD = 4;     // rows of loads kept in flight
+
+// Smoothed Scharr gradient, walking down columns.  Lane l of a warp owns
+// column x = x_w + l - 1 (x_w: the warp's first output column) and the GK
+// output rows y0 .. y0 + GK - 1.  Each needed row of L is staged per warp
+// (columns x_w - 1 - R .. x_w + GCOLS + R, two coalesced loads per lane,
+// issued GPD rows ahead) in a small shared-memory row from which every lane
+// filters its column horizontally with G(sigma_d) (radius R, reflected
+// borders); the last 2R + 1 filtered rows stay in registers for the vertical
+// pass, and the smoothed values S of neighbouring columns come from warp
+// shuffles for the 3x3 Scharr pair ([-1 0 1]/2 x [3 10 3]/16 and its
+// transpose):
+//   Lx(y) = (3 D(y-1) + 10 D(y) + 3 D(y+1)) / 32,  D = S(x+1) - S(x-1)
+//   Ly(y) = (E(y+1) - E(y-1)) / 32,  E = 3 S(x-1) + 10 S(x) + 3 S(x+1).
+// Lanes 0 and 31 only supply S to their neighbours.  MODE_COND writes the
+// conductance g of Eq. 3 (and zeros to `zero` if given); MODE_MAX folds
 // |grad| of interior pixels into a global maximum; MODE_HIST bins the
 // non-zero interior magnitudes.
-// Every pass works on runs of 4 consecutive outputs per thread so each
-// shared-memory value loaded feeds several taps from registers.
 template <int MODE, int R>
-__global__ void __launch_bounds__(BX* BY)
-k_gradient(const float* __restrict__ L, float* __restrict__ g, int pitch, int w, int h,
+__global__ void __launch_bounds__(GWARPS * 32)
+k_gradient(const float* __restrict__ L, float* __restrict__ g, float* __restrict__ zero, int pitch, int w, int h,
            const __grid_constant__ GaussTaps taps, const float* __restrict__ d_k, int diffusivity,
            unsigned int* __restrict__ d_hmax_bits, unsigned int* __restrict__ d_hist, int nbins)
 {
-    constexpr int CW = TX + 2, CH = TY + 2;      // smoothed region (halo 1 for Scharr)
-    constexpr int SW = CW + 2 * R, SH = CH + 2 * R;
-    constexpr int KX = (SW + BX - 1) / BX;
-    constexpr int CWR = (CW + 3) / 4;            // 4-wide runs per row of B / C
-    constexpr int CHR = (CH + 3) / 4;            // 4-high runs per column of C
-    __shared__ float A[SH][SW + 4];  // raw L (+4: runs may read past the edge)
-    __shared__ float B[SH + 4][CW + 4];  // row-smoothed
-    __shared__ float C[CH + 4][CW + 1];  // smoothed
+    constexpr int RW = GCOLS + 2 + 2 * R;  // staged columns per row (<= 64)
+    __shared__ float srow[GWARPS][2][64];
     extern __shared__ unsigned int hist_s[];
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * BX + tx;
-    constexpr int NT = BX * BY;
-
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int xw = (blockIdx.x * GWARPS + warp) * GCOLS;
+    const int x = xw + lane - 1;
+    const int y0 = blockIdx.y * GK;
+    constexpr int NT = GWARPS * 32;
     if (MODE == MODE_HIST) {
-        for (int i = tid; i < nbins; i += NT) hist_s[i] = 0u;
+        for (int i = threadIdx.x; i < nbins; i += NT) hist_s[i] = 0u;
+        __syncthreads();
     }
-    int gx[KX];
+    // the two staged columns of this lane, reflected into the image
+    const int c0 = reflect_index(xw - 1 - R + lane, w);
+    const bool has1 = lane + 32 < RW;
+    const int c1 = reflect_index(xw - 1 - R + lane + 32, w);
+    float wt[R + 1];
 #pragma unroll
-    for (int k = 0; k < KX; ++k) gx[k] = reflect_index(x0 - 1 - R + tx + k * BX, w);
-#pragma unroll
-    for (int sy = ty; sy < SH; sy += BY) {
-        const float* row = L + (size_t)reflect_index(y0 - 1 - R + sy, h) * pitch;
-#pragma unroll
-        for (int k = 0; k < KX; ++k)
-            if (tx + k * BX < SW) A[sy][tx + k * BX] = __ldg(row + gx[k]);
-    }
-    __syncthreads();
-    // rows: B[sy][4u .. 4u+3]
-#pragma unroll
-    for (int t = tid; t < SH * CWR; t += NT) {
-        const int sy = t / CWR, u = t - sy * CWR;
-        float v[4 + 2 * R];
-#pragma unroll
-        for (int j = 0; j < 4 + 2 * R; ++j) v[j] = A[sy][4 * u + j];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float acc = 0.f;
-#pragma unroll
-            for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], v[q + j], acc);
-            B[sy][4 * u + q] = acc;
-        }
-    }
-    __syncthreads();
-    // columns: C[4u .. 4u+3][sx]
-#pragma unroll
-    for (int t = tid; t < CW * CHR; t += NT) {
-        const int u = t / CW, sx = t - u * CW;
-        float v[4 + 2 * R];
-#pragma unroll
-        for (int j = 0; j < 4 + 2 * R; ++j) v[j] = B[4 * u + j][sx];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float acc = 0.f;
-#pragma unroll
-            for (int j = 0; j <= 2 * R; ++j) acc = fmaf(taps.w[j], v[q + j], acc);
-            C[4 * u + q][sx] = acc;
-        }
-    }
-    __syncthreads();
+    for (int j = 0; j <= R; ++j) wt[j] = taps.w[R + j];
 
-    float kk = 0.f, hmax = 0.f;
-    if (MODE == MODE_COND) kk = *d_k;
-    if (MODE == MODE_HIST) hmax = __uint_as_float(*d_hmax_bits);
-    float local_max = 0.f;
-    const float c0 = 3.f / 16.f, c1 = 10.f / 16.f;
-    const int gxo = x0 + tx;
-    const int oy0 = 4 * ty;  // this thread's 4 output rows
-    // C[cy][cx] holds the smoothed value at (x0 - 1 + cx, y0 - 1 + cy)
-    float cm[6], cc[6], cp[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        cm[j] = C[oy0 + j][tx];
-        cc[j] = C[oy0 + j][tx + 1];
-        cp[j] = C[oy0 + j][tx + 2];
+    float inv_k2 = 0.f, hmax_scale = 0.f;
+    if (MODE == MODE_COND) {
+        const float kk = *d_k;
+        inv_k2 = 1.f / (kk * kk);
     }
+    if (MODE == MODE_HIST) hmax_scale = (float)nbins / __uint_as_float(*d_hmax_bits);
+    float local_max = 0.f;
+    const bool out_col = lane >= 1 && lane <= GCOLS && x < w;
+
+    // H rows y0 - 1 - R .. y0 + GK + R; S rows y0 - 1 .. y0 + GK
+    constexpr int NI = GK + 2 + 2 * R;
+    float pre[GPD + 1][2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int gy = y0 + oy0 + q;
-        float lx = c0 * 0.5f * (cp[q] - cm[q]);
-        lx += c1 * 0.5f * (cp[q + 1] - cm[q + 1]);
-        lx += c0 * 0.5f * (cp[q + 2] - cm[q + 2]);
-        float ly = c0 * 0.5f * (cm[q + 2] - cm[q]);
-        ly += c1 * 0.5f * (cc[q + 2] - cc[q]);
-        ly += c0 * 0.5f * (cp[q + 2] - cp[q]);
-        if (gxo >= w || gy >= h) continue;
-        if (MODE == MODE_COND) {
-            const float qv = (lx * lx + ly * ly) / (kk * kk);
-            g[(size_t)gy * pitch + gxo] = diffusivity == KAZE_G1 ? expf(-qv) : 1.f / (1.f + qv);
-        } else {
-            const bool interior = gxo >= 1 && gxo <= w - 2 && gy >= 1 && gy <= h - 2;
-            if (!interior) continue;
-            const float m = sqrtf(lx * lx + ly * ly);
-            if (MODE == MODE_MAX) {
-                local_max = fmaxf(local_max, m);
-            } else if (m > 0.f) {
-                int b = (int)floorf((float)nbins * m / hmax);
-                b = min(b, nbins - 1);
-                atomicAdd(&hist_s[b], 1u);
+    for (int i = 0; i < GPD && i < NI; ++i) {
+        const float* row = L + (size_t)reflect_index(y0 - 1 - R + i, h) * pitch;
+        pre[i][0] = __ldg(row + c0);
+        pre[i][1] = has1 ? __ldg(row + c1) : 0.f;
+    }
+    float hw[2 * R + 1];      // last 2R + 1 horizontally filtered rows
+    float dm = 0.f, d0 = 0.f, em = 0.f, e0 = 0.f;  // D, E of the two previous S rows
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        if (i + GPD < NI) {
+            const float* row = L + (size_t)reflect_index(y0 - 1 - R + i + GPD, h) * pitch;
+            pre[(i + GPD) % (GPD + 1)][0] = __ldg(row + c0);
+            pre[(i + GPD) % (GPD + 1)][1] = has1 ? __ldg(row + c1) : 0.f;
+        }
+        float* sr_ = srow[warp][i & 1];
+        sr_[lane] = pre[i % (GPD + 1)][0];
+        if (has1) sr_[lane + 32] = pre[i % (GPD + 1)][1];
+        __syncwarp();
+        const float* v = sr_ + lane;  // v[R] is this lane's column
+        float hv = wt[0] * v[R];
+#pragma unroll
+        for (int j = 1; j <= R; ++j) hv = fmaf(wt[j], v[R - j] + v[R + j], hv);
+#pragma unroll
+        for (int j = 0; j < 2 * R; ++j) hw[j] = hw[j + 1];
+        hw[2 * R] = hv;
+        if (i < 2 * R) continue;
+        // S at row y0 - 1 + (i - 2R)
+        float sv = wt[0] * hw[R];
+#pragma unroll
+        for (int j = 1; j <= R; ++j) sv = fmaf(wt[j], hw[R - j] + hw[R + j], sv);
+        const float sl = __shfl_up_sync(0xffffffffu, sv, 1);
+        const float sr = __shfl_down_sync(0xffffffffu, sv, 1);
+        // explicit fmaf: the batched kernel (k_batch.cu) repeats this
+        // arithmetic operation for operation, so both paths agree bit for bit
+        const float dp = sr - sl;
+        const float ep = fmaf(10.f, sv, 3.f * (sl + sr));
+        const int si = i - 2 * R;
+        if (si >= 2) {
+            const int y = y0 + si - 2;  // output row: S rows y - 1, y, y + 1
+            const float lx = fmaf(10.f, d0, 3.f * (dm + dp)) * (1.f / 32.f);
+            const float ly = (ep - em) * (1.f / 32.f);
+            const float m2 = fmaf(ly, ly, lx * lx);
+            if (out_col && y < h) {
+                if (MODE == MODE_COND) {
+                    const float qv = m2 * inv_k2;
+                    g[(size_t)y * pitch + x] = diffusivity == KAZE_G1 ? expf(-qv) : __fdividef(1.f, 1.f + qv);
+                    if (zero) zero[(size_t)y * pitch + x] = 0.f;
+                } else if (x >= 1 && x <= w - 2 && y >= 1 && y <= h - 2) {
+                    const float m = sqrtf(m2);
+                    if (MODE == MODE_MAX) {
+                        local_max = fmaxf(local_max, m);
+                    } else if (m > 0.f) {
+                        int b = (int)floorf(m * hmax_scale);
+                        b = min(b, nbins - 1);
+                        atomicAdd(&hist_s[b], 1u);
+                    }
+                }
             }
         }
+        dm = d0;
+        d0 = dp;
+        em = e0;
+        e0 = ep;
     }
     if (MODE == MODE_MAX) {
         for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
         // non-negative floats order like their bit patterns
-        if (tx == 0 && local_max > 0.f) atomicMax(d_hmax_bits, __float_as_uint(local_max));
+        if (lane == 0 && local_max > 0.f) atomicMax(d_hmax_bits, __float_as_uint(local_max));
     }
     if (MODE == MODE_HIST) {
         __syncthreads();
-        for (int i = tid; i < nbins; i += NT) {
+        for (int i = threadIdx.x; i < nbins; i += NT) {
             const unsigned int v = hist_s[i];
             if (v) atomicAdd(&d_hist[i], v);
         }
@@ -240,25 +248,25 @@ __global__ void k_percentile(const unsigned int* __restrict__ hist, int nbins,
 __global__ void k_set_scalar(float* d, float v) { *d = v; }
 
 template <int MODE, int R>
-cudaError_t launch_gradient_r(const float* L, float* g, int pitch, int w, int h, const GaussTaps& taps,
+cudaError_t launch_gradient_r(const float* L, float* g, float* zero, int pitch, int w, int h, const GaussTaps& taps,
                               const float* d_k, int diffusivity, unsigned int* hmax_bits, unsigned int* hist,
                               int nbins, cudaStream_t st)
 {
-    dim3 grid((w + TX - 1) / TX, (h + TY - 1) / TY);
+    dim3 grid((w + GWARPS * GCOLS - 1) / (GWARPS * GCOLS), (h + GK - 1) / GK);
     const size_t smem = MODE == MODE_HIST ? (size_t)nbins * sizeof(unsigned int) : 0;
-    k_gradient<MODE, R><<<grid, dim3(BX, BY), smem, st>>>(L, g, pitch, w, h, taps, d_k, diffusivity, hmax_bits,
-                                                         hist, nbins);
+    k_gradient<MODE, R><<<grid, GWARPS * 32, smem, st>>>(L, g, zero, pitch, w, h, taps, d_k, diffusivity,
+                                                         hmax_bits, hist, nbins);
     return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t launch_gradient(const float* L, float* g, int pitch, int w, int h, const GaussTaps& taps,
+cudaError_t launch_gradient(const float* L, float* g, float* zero, int pitch, int w, int h, const GaussTaps& taps,
                             const float* d_k, int diffusivity, unsigned int* hmax_bits, unsigned int* hist,
                             int nbins, cudaStream_t st)
 {
     switch (taps.r) {
 #define KZ_GRAD_CASE(RR) \
-    case RR: return launch_gradient_r<MODE, RR>(L, g, pitch, w, h, taps, d_k, diffusivity, hmax_bits, hist, nbins, st);
+    case RR: return launch_gradient_r<MODE, RR>(L, g, zero, pitch, w, h, taps, d_k, diffusivity, hmax_bits, hist, nbins, st);
         KZ_GRAD_CASE(1) KZ_GRAD_CASE(2) KZ_GRAD_CASE(3) KZ_GRAD_CASE(4) KZ_GRAD_CASE(5) KZ_GRAD_CASE(6)
 #undef KZ_GRAD_CASE
         default: return cudaErrorInvalidValue;
@@ -296,23 +304,23 @@ cudaError_t launch_gaussian(const float* in, int in_pitch, float* out, int out_p
     }
 }
 
-cudaError_t launch_conductance(const float* L, float* g, int pitch, int w, int h, const GaussTaps& taps,
-                               const float* d_k, int diffusivity, cudaStream_t st)
+cudaError_t launch_conductance(const float* L, float* g, float* zero_out, int pitch, int w, int h,
+                               const GaussTaps& taps, const float* d_k, int diffusivity, cudaStream_t st)
 {
-    return launch_gradient<MODE_COND>(L, g, pitch, w, h, taps, d_k, diffusivity, nullptr, nullptr, 0, st);
+    return launch_gradient<MODE_COND>(L, g, zero_out, pitch, w, h, taps, d_k, diffusivity, nullptr, nullptr, 0, st);
 }
 
 cudaError_t launch_grad_max(const float* L, int pitch, int w, int h, const GaussTaps& taps,
                             unsigned int* d_hmax_bits, cudaStream_t st)
 {
-    return launch_gradient<MODE_MAX>(L, nullptr, pitch, w, h, taps, nullptr, 0, d_hmax_bits, nullptr, 0, st);
+    return launch_gradient<MODE_MAX>(L, nullptr, nullptr, pitch, w, h, taps, nullptr, 0, d_hmax_bits, nullptr, 0, st);
 }
 
 cudaError_t launch_grad_hist(const float* L, int pitch, int w, int h, const GaussTaps& taps,
                              const unsigned int* d_hmax_bits, unsigned int* d_hist, int nbins,
                              cudaStream_t st)
 {
-    return launch_gradient<MODE_HIST>(L, nullptr, pitch, w, h, taps, nullptr, 0,
+    return launch_gradient<MODE_HIST>(L, nullptr, nullptr, pitch, w, h, taps, nullptr, 0,
                                       const_cast<unsigned int*>(d_hmax_bits), d_hist, nbins, st);
 }
 

@@ -36,6 +36,10 @@ struct kaze_handle {
     kaze_options opt;
     int max_w = 0, max_h = 0, N = 0;
     cudaStream_t stream = nullptr;
+    // second stream for the column half of each AOS step, with the events
+    // that fork it off and join it back to `stream`
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // device arena and its parts
     void* arena = nullptr;
@@ -79,7 +83,11 @@ struct kaze_handle {
     int launches = 0;
     int graph_launches = 0;
     bool profiling = false;
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+    struct ProfEntry {
+        int kind, kernels;
+        cudaEvent_t start, stop;
+    };
+    std::vector<ProfEntry> prof;
 
     std::vector<kaze_keypoint> hkp;
     std::string err;
@@ -114,23 +122,26 @@ kaze_status cuda_fail(kaze_handle* h, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);      \
     } while (0)
 
-// Enqueue one kernel of the given kind, counting it and, while profiling,
-// bracketing it with an event pair on the handle's stream.
-#define KZ_LAUNCH(h, kind, call)                                                   \
+// Enqueue `nk` kernels of the given kind with one launcher call, counting
+// them and, while profiling, bracketing the call with an event pair on the
+// handle's stream (external records: inside a stream capture they become
+// event-record nodes of the graph, which is what timing needs).
+#define KZ_LAUNCH_N(h, kind, nk, call)                                             \
     do {                                                                           \
         cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;                                \
         if ((h)->profiling) {                                                      \
             KZ_TRY(h, cudaEventCreate(&ev0_));                                     \
             KZ_TRY(h, cudaEventCreate(&ev1_));                                     \
-            KZ_TRY(h, cudaEventRecord(ev0_, (h)->stream));                         \
+            KZ_TRY(h, cudaEventRecordWithFlags(ev0_, (h)->stream, cudaEventRecordExternal)); \
         }                                                                          \
         KZ_TRY(h, call);                                                           \
-        (h)->launches += 1;                                                        \
+        (h)->launches += (nk);                                                     \
         if ((h)->profiling) {                                                      \
-            KZ_TRY(h, cudaEventRecord(ev1_, (h)->stream));                         \
-            (h)->prof.push_back({(kind), {ev0_, ev1_}});                           \
+            KZ_TRY(h, cudaEventRecordWithFlags(ev1_, (h)->stream, cudaEventRecordExternal)); \
+            (h)->prof.push_back({(kind), (nk), ev0_, ev1_});                       \
         }                                                                          \
     } while (0)
+#define KZ_LAUNCH(h, kind, call) KZ_LAUNCH_N(h, kind, 1, call)
 
 #define KZ_CHECK(st) \
     do {                                   \
@@ -211,8 +222,9 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
         const float* Lp = level_ptr(h, i - 1);
         float* Li = level_ptr(h, i);
         const float tau = (float)(h->t[i] - h->t[i - 1]);
-        KZ_LAUNCH(h, KK_CONDUCTANCE, kz::launch_conductance(Lp, h->g, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
         if (h->surrogate) {
+            KZ_LAUNCH(h, KK_CONDUCTANCE,
+                      kz::launch_conductance(Lp, h->g, nullptr, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
             kz::sg::Samples S;
             std::memset(&S, 0, sizeof(S));
             S.L[0] = Lp;
@@ -227,8 +239,23 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
             KZ_LAUNCH(h, KK_SURROGATE, kz::sg::enqueue_pipeline_step(h->surrogate, S, st));
             continue;
         }
-        KZ_LAUNCH(h, KK_AOS_ROWS, kz::launch_aos_rows(Lp, h->g, h->ux, P, w, hh, tau, h->d_status, st));
-        KZ_LAUNCH(h, KK_AOS_COLS, kz::launch_aos_cols(Lp, h->g, h->ux, Li, P, w, hh, tau, h->d_status, st));
+        // conductance also zeroes L_i; the row and column halves of the AOS
+        // step then add into it, concurrently on two streams (one stream
+        // while profiling, so that events bracket single kernels)
+        KZ_LAUNCH(h, KK_CONDUCTANCE,
+                  kz::launch_conductance(Lp, h->g, Li, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
+        const bool fork = !h->profiling && h->side != nullptr;
+        if (fork) {
+            KZ_TRY(h, cudaEventRecord(h->ev_fork, st));
+            KZ_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        }
+        KZ_LAUNCH(h, KK_AOS_ROWS, kz::launch_aos_rows(Lp, h->g, nullptr, Li, P, w, hh, tau, h->d_status, st));
+        KZ_LAUNCH(h, KK_AOS_COLS,
+                  kz::launch_aos_cols(Lp, h->g, nullptr, Li, P, w, hh, tau, h->d_status, fork ? h->side : st));
+        if (fork) {
+            KZ_TRY(h, cudaEventRecord(h->ev_join, h->side));
+            KZ_TRY(h, cudaStreamWaitEvent(st, h->ev_join, 0));
+        }
     }
     h->built = true;
     h->responded = false;
@@ -237,8 +264,9 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
 
 kaze_status enqueue_response(kaze_handle* h)
 {
-    KZ_LAUNCH(h, KK_DOH, kz::launch_doh(h->levels, h->doh, h->cur_pitch, h->cur_plane, h->cur_w, h->cur_h, 0, h->N,
-                             h->tab, h->stream));
+    KZ_LAUNCH_N(h, KK_DOH, kz::doh_launches(h->tab, 0, h->N),
+                kz::launch_doh(h->levels, h->doh, h->cur_pitch, h->cur_plane, h->cur_w, h->cur_h, 0, h->N, h->tab,
+                               h->stream));
     h->responded = true;
     return KAZE_OK;
 }
@@ -247,7 +275,7 @@ kaze_status enqueue_extrema(kaze_handle* h, const float* D, int pitch, long long
                             const kz::LevelTable& tab)
 {
     KZ_TRY(h, cudaMemsetAsync(h->d_count, 0, sizeof(unsigned int), h->stream));
-    KZ_LAUNCH(h, KK_EXTREMA, kz::launch_extrema(D, pitch, plane, w, hh, n, tab, h->opt.dthreshold, h->opt.edge_r, h->d_kp,
+    KZ_LAUNCH_N(h, KK_EXTREMA, n >= 3 ? 1 : 0, kz::launch_extrema(D, pitch, plane, w, hh, n, tab, h->opt.dthreshold, h->opt.edge_r, h->d_kp,
                                  h->opt.max_keypoints, h->d_count, h->stream));
     KZ_TRY(h, cudaMemcpyAsync(h->h_count, h->d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
     KZ_TRY(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -357,7 +385,7 @@ kaze_status handle_enqueue_into(kaze_handle* h, const float* d_img, int w, int h
     h->doh = own_doh;
     KZ_CHECK(s);
     KZ_TRY(h, cudaMemsetAsync(d_count, 0, sizeof(unsigned int), h->stream));
-    KZ_LAUNCH(h, KK_EXTREMA, kz::launch_extrema(doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab,
+    KZ_LAUNCH_N(h, KK_EXTREMA, h->N >= 3 ? 1 : 0, kz::launch_extrema(doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab,
                                                 h->opt.dthreshold, h->opt.edge_r, d_kp, cap, d_count, h->stream));
     h->built = false;  // the handle's own buffers were not written
     h->responded = false;
@@ -499,6 +527,12 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     *h->h_count = 0;
     h->h_status = (int*)(h->h_count + 1);
     *h->h_status = 0;
+    if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+        kaze_destroy(h);
+        return create_fail(KAZE_ERR_CUDA, std::string("stream / event creation: ") + cudaGetErrorName(e));
+    }
     *out = h;
     return KAZE_OK;
 }
@@ -640,7 +674,7 @@ KAZE_API kaze_status kaze_op_conductance(kaze_handle* h, const float* d_L, float
     KZ_CHECK(check_image(h, w, hh));
     if (pitch < w || !(k > 0.f)) return fail(h, KAZE_ERR_INVALID_ARG, "bad pitch or k");
     KZ_TRY(h, kz::launch_set_scalar(h->d_k, k, h->stream));
-    KZ_TRY(h, kz::launch_conductance(d_L, d_g, pitch, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, h->stream));
+    KZ_TRY(h, kz::launch_conductance(d_L, d_g, nullptr, pitch, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, h->stream));
     return KAZE_OK;
 }
 
@@ -656,7 +690,7 @@ KAZE_API kaze_status kaze_op_aos_step(kaze_handle* h, const float* d_Lprev, cons
         return fail(h, KAZE_ERR_INVALID_ARG, "outputs alias inputs");
     if (!(tau >= 0.f)) return fail(h, KAZE_ERR_INVALID_ARG, "negative tau");
     KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
-    KZ_TRY(h, kz::launch_aos_rows(d_Lprev, d_g, d_ux, pitch, w, hh, tau, h->d_status, h->stream));
+    KZ_TRY(h, kz::launch_aos_rows(d_Lprev, d_g, d_ux, nullptr, pitch, w, hh, tau, h->d_status, h->stream));
     KZ_TRY(h, kz::launch_aos_cols(d_Lprev, d_g, d_ux, d_Lnext, pitch, w, hh, tau, h->d_status, h->stream));
     KZ_TRY(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     KZ_TRY(h, cudaStreamSynchronize(h->stream));
@@ -736,25 +770,42 @@ KAZE_API kaze_status kaze_profile(kaze_handle* h, const float* d_img, int w, int
         h_ms[k] = 0.0;
         h_launches[k] = 0;
     }
+    // The launch sequence with an event pair around every kernel; on a
+    // capturable stream it is recorded as a graph and replayed twice (the
+    // events keep the second replay's times), so the kernels are timed as a
+    // detection runs them.  The default streams replay nothing: eager timing.
+    const bool capture = !(h->stream == nullptr || h->stream == cudaStreamLegacy || h->stream == cudaStreamPerThread);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
     h->profiling = true;
     h->launches = 0;
+    if (capture) KZ_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     kaze_status s = enqueue_build(h, d_img, w, hh, pitch_elems);
     if (s == KAZE_OK) s = enqueue_response(h);
     if (s == KAZE_OK) s = enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab);
     h->profiling = false;
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaError_t e = cudaSuccess;
+    if (capture) {
+        e = cudaStreamEndCapture(h->stream, &graph);
+        if (s == KAZE_OK && e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+        for (int r = 0; r < 2 && s == KAZE_OK && e == cudaSuccess; ++r) e = cudaGraphLaunch(gexec, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
     for (auto& p : h->prof) {
         float ms = 0.f;
-        if (s == KAZE_OK && e == cudaSuccess && cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
-            h_ms[p.first] += ms;
-            h_launches[p.first] += 1;
+        if (s == KAZE_OK && e == cudaSuccess) {
+            e = cudaEventElapsedTime(&ms, p.start, p.stop);
+            h_ms[p.kind] += ms;
+            h_launches[p.kind] += p.kernels;
         }
-        cudaEventDestroy(p.second.first);
-        cudaEventDestroy(p.second.second);
+        cudaEventDestroy(p.start);
+        cudaEventDestroy(p.stop);
     }
     h->prof.clear();
     if (s != KAZE_OK) return s;
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    if (e != cudaSuccess) return cuda_fail(h, e, "kaze_profile (graph replay or event timing)");
     return KAZE_OK;
 }
 
@@ -784,5 +835,8 @@ KAZE_API void kaze_destroy(kaze_handle* h)
     drop_graph(h);
     if (h->arena) cudaFree(h->arena);
     if (h->h_count) cudaFreeHost(h->h_count);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
     delete h;
 }

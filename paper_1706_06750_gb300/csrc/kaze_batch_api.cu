@@ -377,7 +377,7 @@ KAZE_API kaze_status kaze_batch_create(const kaze_options* opt, int n, const int
             }
             P.tab.norm[i] = (float)norm;
             const double d = 1024.0 * st * st;
-            P.doh_scale[i] = (float)(norm / (d * d));
+            P.doh_scale[i] = (float)((double)P.tab.norm[i] / (d * d));  // as the single-image kernel does
             P.tau[i] = i > 0 ? (float)(t[i] - t[i - 1]) : 0.f;
         }
     P.pct = o.k_percentile;

@@ -40,6 +40,27 @@ __host__ __device__ __forceinline__ int reflect_index(int i, int n)
     return r < n ? r : p - 1 - r;
 }
 
+// Response arithmetic of Eq. 8 shared by the single-image and batched
+// kernels (explicit fmaf, so both give the same bits).  One lattice row
+// (taps at -2s .. 2s): the x-derivative pair [1 0 -2 0 1], the smoothing
+// [9 60 118 60 9] and the first derivative [-3 -10 0 10 3].
+__device__ __forceinline__ void doh_lattice_row(float v0, float v1, float v2, float v3, float v4, float& hd,
+                                                float& hs, float& hx)
+{
+    hd = fmaf(-2.f, v2, v0 + v4);
+    hs = fmaf(118.f, v2, fmaf(60.f, v1 + v3, 9.f * (v0 + v4)));
+    hx = fmaf(10.f, v3 - v1, 3.f * (v4 - v0));
+}
+
+// The determinant from five consecutive filtered lattice rows a[0..4].
+__device__ __forceinline__ float doh_value(const float* hd, const float* hs, const float* hx, float scale)
+{
+    const float lxx = fmaf(118.f, hd[2], fmaf(60.f, hd[1] + hd[3], 9.f * (hd[0] + hd[4])));
+    const float lyy = fmaf(-2.f, hs[2], hs[0] + hs[4]);
+    const float lxy = fmaf(10.f, hx[3] - hx[1], 3.f * (hx[4] - hx[0]));
+    return scale * fmaf(lxx, lyy, -(lxy * lxy));
+}
+
 // Raises a kernel's dynamic shared-memory limit to what the device allows
 // beside the kernel's static shared memory.
 template <typename F>
@@ -67,7 +88,9 @@ cudaError_t configure_detector_kernels();
 cudaError_t launch_gaussian(const float* in, int in_pitch, float* out, int out_pitch,
                             int w, int h, const GaussTaps& taps, cudaStream_t st);
 
-cudaError_t launch_conductance(const float* L, float* g, int pitch, int w, int h,
+// g of Eq. 3 from L; if zero_out is not null it also receives zeros at the
+// same pixels (the accumulation target of the next AOS step).
+cudaError_t launch_conductance(const float* L, float* g, float* zero_out, int pitch, int w, int h,
                                const GaussTaps& taps, const float* d_k, int diffusivity,
                                cudaStream_t st);
 
@@ -83,17 +106,25 @@ cudaError_t launch_percentile(const unsigned int* d_hist, int nbins,
                               cudaStream_t st);
 cudaError_t launch_set_scalar(float* d_dst, float value, cudaStream_t st);
 
-// AOS step of Eq. 4: rows (writes ux), then columns + average (writes Lnext).
-// Rows need 16-byte aligned rows (pitch % 4 == 0); columns are staged by TMA
-// tensor copies.  A bounded wait that runs out sets bit 0 of *d_status.
-cudaError_t launch_aos_rows(const float* L, const float* g, float* ux, int pitch,
+// AOS step of Eq. 4, L_next = (u_x + u_y) / 2.  Either sequentially: rows
+// write u_x to ux (acc == nullptr), then columns read it and write Lnext; or
+// as two independent halves that may run concurrently: with Lnext zeroed
+// beforehand, rows add u_x / 2 into acc == Lnext and columns (ux == nullptr)
+// add u_y / 2 into Lnext (two addends onto zero: the same sum in either
+// order).  Rows need 16-byte aligned rows (pitch % 4 == 0); columns are
+// staged by TMA tensor copies.  A bounded wait that runs out sets bit 0 of
+// *d_status.
+cudaError_t launch_aos_rows(const float* L, const float* g, float* ux, float* acc, int pitch,
                             int w, int h, float tau, int* d_status, cudaStream_t st);
+// cols: columns per CTA (4 or 8); 0 picks the widest that fits.
 cudaError_t launch_aos_cols(const float* L, const float* g, const float* ux, float* Lnext,
-                            int pitch, int w, int h, float tau, int* d_status, cudaStream_t st);
+                            int pitch, int w, int h, float tau, int* d_status, cudaStream_t st, int cols = 0);
 size_t aos_rows_smem_bytes(int w);
 size_t aos_cols_smem_bytes(int h);
 
 // Detector response of Eq. 8 for levels [l0, l0 + nl) of a level stack.
+// Number of kernels launch_doh issues for levels l0 .. l0 + nl - 1.
+int doh_launches(const LevelTable& tab, int l0, int nl);
 cudaError_t launch_doh(const float* L, float* D, int pitch, long long plane_stride,
                        int w, int h, int l0, int nl, const LevelTable& tab, cudaStream_t st);
 

@@ -69,7 +69,7 @@ KAZE_API kaze_status kaze_aos_step_static(const float* d_Lprev, const float* d_g
     // the array keeps the previous call's contents: the status word must
     // start at zero, the row solution is overwritten before it is read
     if (cudaMemsetAsync(s->status, 0, sizeof(int), stream) != cudaSuccess) return KAZE_ERR_CUDA;
-    if (kz::launch_aos_rows(d_Lprev, d_g, s->ux, pitch, w, h, tau, s->status, stream) != cudaSuccess)
+    if (kz::launch_aos_rows(d_Lprev, d_g, s->ux, nullptr, pitch, w, h, tau, s->status, stream) != cudaSuccess)
         return KAZE_ERR_CUDA;
     if (kz::launch_aos_cols(d_Lprev, d_g, s->ux, d_Lnext, pitch, w, h, tau, s->status, stream) != cudaSuccess)
         return KAZE_ERR_CUDA;
