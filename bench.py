@@ -161,29 +161,40 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_digest():
+# source files of each kernel kind (with the helpers they include)
+KIND_SOURCES = {
+    "presmooth": ["k_filters.cu"], "grad_max": ["k_filters.cu"], "grad_hist": ["k_filters.cu"],
+    "percentile": ["k_filters.cu"], "conductance": ["k_filters.cu"],
+    "aos_rows": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
+    "aos_cols": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
+    "doh": ["k_detector.cu"], "extrema": ["k_detector.cu"],
+}
+
+
+def kernel_source_digest(kind):
+    """Digest of the sources a kernel kind is built from (its files and the
+    shared internal header)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1706_06750_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".h", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in sorted(set(KIND_SOURCES.get(kind, [])) | {"kaze_internal.h"}):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kind):
     """DRAM bytes per launch of `kind` from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+    taken on the kind's current sources (else None).  The summary's table rows
+    read | kind | kernel | bytes per launch | source digest | ..."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
     try:
         text = open(path).read()
     except OSError:
         return None
-    m = re.search(r"kernel_source_digest:\s*([0-9a-f]+)", text)
-    if not m or m.group(1) != kernel_source_digest():
+    m = re.search(rf"^\|\s*{re.escape(kind)}\s*\|[^|]*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]+)\s*\|", text, re.M)
+    if not m or m.group(2) != kernel_source_digest(kind):
         return None
-    m = re.search(rf"^\|\s*{re.escape(kind)}\s*\|[^|]*\|\s*([0-9.eE+]+)\s*\|", text, re.M)
-    return float(m.group(1)) if m else None
+    return float(m.group(1))
 
 
 # ------------------------------------------------------------------ oracle --
