@@ -318,8 +318,9 @@ kaze_status kaze_aos_step_static(const float* d_Lprev, const float* d_g, float* 
 #define KAZE_SURROGATE_PARAMS 20257
 #define KAZE_SURROGATE_MAX_SAMPLES 64
 #define KAZE_SURROGATE_TRAIN 1   /* create flag: allocate training buffers      */
-#define KAZE_SURROGATE_FUSED 0   /* step path: whole network in one kernel     */
-#define KAZE_SURROGATE_LAYERED 1 /* step path: one kernel per layer (TRAIN)    */
+#define KAZE_SURROGATE_FUSED 0      /* step path: whole network in one kernel, tcgen05 */
+#define KAZE_SURROGATE_LAYERED 1    /* step path: one kernel per layer (TRAIN)         */
+#define KAZE_SURROGATE_FUSED_SYNC 2 /* step path: one kernel on mma.sync (cross-check)  */
 
 typedef struct kaze_surrogate kaze_surrogate;
 
@@ -341,12 +342,20 @@ kaze_status kaze_surrogate_get_params(kaze_surrogate* s, float* h_params, int co
 kaze_status kaze_surrogate_set_params(kaze_surrogate* s, const float* h_params, int count);
 
 /* d_out[i] = L_next of sample i (asynchronous).  path KAZE_SURROGATE_FUSED
- * runs one persistent kernel; KAZE_SURROGATE_LAYERED runs the layer kernels
- * of training (needs KAZE_SURROGATE_TRAIN and sizes within the maximum).
- * d_out[i] must not overlap d_L[j] or d_g[j] (equal pointers are rejected). */
+ * runs one persistent kernel on the tcgen05 tensor cores (accumulators in
+ * tensor memory); KAZE_SURROGATE_FUSED_SYNC the same network in one kernel
+ * on mma.sync; KAZE_SURROGATE_LAYERED the layer kernels of training (needs
+ * KAZE_SURROGATE_TRAIN and sizes within the maximum).  The three agree to
+ * FP32 summation order.  d_out[i] must not overlap d_L[j] or d_g[j] (equal
+ * pointers are rejected). */
 kaze_status kaze_surrogate_step(kaze_surrogate* s, const float* const* d_L, const float* const* d_g,
                                 const float* h_tau, float* const* d_out, int n, int w, int h_, int pitch,
                                 int path);
+
+/* Waits for the surrogate's stream; KAZE_ERR_TIMEOUT (and the flag cleared)
+ * if a bounded device-side wait of a fused step ran out since the last
+ * call. */
+kaze_status kaze_surrogate_sync(kaze_surrogate* s);
 
 /* Loss and its gradient with respect to the parameters (h_grad: host,
  * KAZE_SURROGATE_PARAMS values) for targets d_T; h_loss may be NULL.

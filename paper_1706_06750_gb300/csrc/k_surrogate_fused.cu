@@ -251,6 +251,7 @@ cudaError_t configure_surrogate_kernels()
     cudaError_t e = cudaFuncSetAttribute((const void*)k_surrogate_fused,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM);
     if (e != cudaSuccess) return e;
+    if ((e = configure_surrogate_tc()) != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

@@ -236,7 +236,7 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
             S.h = hh;
             S.pitch = P;
             S.opitch = P;
-            KZ_LAUNCH(h, KK_SURROGATE, kz::sg::enqueue_pipeline_step(h->surrogate, S, st));
+            KZ_LAUNCH(h, KK_SURROGATE, kz::sg::enqueue_pipeline_step(h->surrogate, S, h->d_status, st));
             continue;
         }
         // conductance also zeroes L_i; the row and column halves of the AOS

@@ -46,6 +46,8 @@ struct kaze_surrogate {
     double* loss_part = nullptr;
     double* d_loss = nullptr;
     double* h_loss = nullptr;  // pinned
+    int* d_status = nullptr;   // bit 0: a bounded device wait of the tcgen05 kernel ran out
+    int* h_status = nullptr;   // pinned
 
     int launches = 0;
     std::string err;
@@ -244,9 +246,9 @@ float input_scale(double tau) { return bf16_value(std::log1p(tau) / 5.0); }
 
 // The detection pipeline's hook (kaze_api.cu): one surrogate step of the
 // fused kernel on the given stream.
-cudaError_t enqueue_pipeline_step(const kaze_surrogate* s, const Samples& S, cudaStream_t st)
+cudaError_t enqueue_pipeline_step(const kaze_surrogate* s, const Samples& S, int* status, cudaStream_t st)
 {
-    return launch_forward_fused(s->pb, s->p, S, st);
+    return launch_forward_tc(s->pb, s->p, S, status, st);
 }
 
 }  // namespace sg
@@ -281,6 +283,9 @@ KAZE_API kaze_status kaze_surrogate_create(int max_w, int max_h, int max_samples
     };
     cudaError_t e = kz::sg::configure_surrogate_kernels();
     if (e != cudaSuccess) return bail(KAZE_ERR_CUDA, std::string("configure: ") + cudaGetErrorString(e));
+    if (cudaMalloc(&s->d_status, sizeof(int)) != cudaSuccess || cudaMemset(s->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&s->h_status, sizeof(int)) != cudaSuccess)
+        return bail(KAZE_ERR_OOM, "status allocation failed");
     if (cudaMalloc(&s->p, sizeof(float) * kParamsPadded) != cudaSuccess ||
         cudaMalloc(&s->grad, sizeof(float) * kParamsPadded) != cudaSuccess ||
         cudaMalloc(&s->m, sizeof(float) * kParamsPadded) != cudaSuccess ||
@@ -371,7 +376,7 @@ KAZE_API kaze_status kaze_surrogate_step(kaze_surrogate* s, const float* const* 
                                          int path)
 {
     if (!s) return KAZE_ERR_INVALID_ARG;
-    if (path != KAZE_SURROGATE_FUSED && path != KAZE_SURROGATE_LAYERED)
+    if (path != KAZE_SURROGATE_FUSED && path != KAZE_SURROGATE_LAYERED && path != KAZE_SURROGATE_FUSED_SYNC)
         return sfail(s, KAZE_ERR_INVALID_ARG, "unknown path");
     if (!d_out) return sfail(s, KAZE_ERR_INVALID_ARG, "NULL output array");
     kz::sg::Samples S;
@@ -383,8 +388,10 @@ KAZE_API kaze_status kaze_surrogate_step(kaze_surrogate* s, const float* const* 
         const kz::sg::Net net = net_of(s);
         SG_LAUNCH(s, 1, kz::sg::launch_features(S, s->x0, s->stream));
         SG_LAUNCH(s, 4, kz::sg::launch_forward(net, S, s->x0, s->a1, s->a2, s->a3, s->stream));
-    } else {
+    } else if (path == KAZE_SURROGATE_FUSED_SYNC) {
         SG_LAUNCH(s, 1, kz::sg::launch_forward_fused(s->pb, s->p, S, s->stream));
+    } else {
+        SG_LAUNCH(s, 1, kz::sg::launch_forward_tc(s->pb, s->p, S, s->d_status, s->stream));
     }
     return KAZE_OK;
 }
@@ -419,6 +426,18 @@ KAZE_API kaze_status kaze_surrogate_train_step(kaze_surrogate* s, const float* c
     s->steps += 1;
     SG_LAUNCH(s, 1, kz::sg::launch_adam(s->p, s->grad, s->m, s->v, s->pb, kParamsPadded, lr, s->steps, s->stream));
     return read_loss(s, h_loss);
+}
+
+KAZE_API kaze_status kaze_surrogate_sync(kaze_surrogate* s)
+{
+    if (!s) return KAZE_ERR_INVALID_ARG;
+    SG_TRY(s, cudaMemcpyAsync(s->h_status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    SG_TRY(s, cudaStreamSynchronize(s->stream));
+    if (*s->h_status) {
+        SG_TRY(s, cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream));
+        return sfail(s, KAZE_ERR_TIMEOUT, "a bounded device-side wait ran out");
+    }
+    return KAZE_OK;
 }
 
 KAZE_API kaze_status kaze_surrogate_steps_taken(const kaze_surrogate* s, long long* steps)
@@ -498,6 +517,8 @@ KAZE_API void kaze_surrogate_destroy(kaze_surrogate* s)
     cudaFree(s->v);
     cudaFree(s->pb);
     cudaFree(s->arena);
+    cudaFree(s->d_status);
     if (s->h_loss) cudaFreeHost(s->h_loss);
+    if (s->h_status) cudaFreeHost(s->h_status);
     delete s;
 }

@@ -80,8 +80,13 @@ cudaError_t launch_features(const Samples& S, __nv_bfloat16* x0, cudaStream_t st
 cudaError_t launch_forward(const Net& net, const Samples& S, const __nv_bfloat16* x0, __nv_bfloat16* a1,
                            __nv_bfloat16* a2, __nv_bfloat16* a3, cudaStream_t st);
 // One kernel for the whole network (inference): no activations in HBM.
-// wpad / ppad: padded BF16 and FP32 parameter vectors.
+// wpad / ppad: padded BF16 and FP32 parameter vectors.  launch_forward_tc
+// runs it on the tcgen05 tensor cores (a bounded wait that runs out sets bit
+// 0 of *status); launch_forward_fused on mma.sync.
+cudaError_t launch_forward_tc(const __nv_bfloat16* wpad, const float* ppad, const Samples& S, int* status,
+                              cudaStream_t st);
 cudaError_t launch_forward_fused(const __nv_bfloat16* wpad, const float* ppad, const Samples& S, cudaStream_t st);
+cudaError_t configure_surrogate_tc();
 cudaError_t configure_surrogate_kernels();
 // Loss partials per CTA (double) and dL/dy (BF16, 8 channels).
 int loss_blocks(int w, int h, int n);
@@ -96,8 +101,9 @@ cudaError_t launch_to_bf16(const float* p, __nv_bfloat16* pb, int count, cudaStr
 
 // The network's step input s = log(1 + tau) / 5, rounded to BF16 on the host.
 float input_scale(double tau);
-// One fused surrogate step of the detection pipeline (kaze_api.cu).
-cudaError_t enqueue_pipeline_step(const kaze_surrogate* s, const Samples& S, cudaStream_t st);
+// One fused surrogate step of the detection pipeline (kaze_api.cu); a
+// device-side timeout sets bit 0 of *status.
+cudaError_t enqueue_pipeline_step(const kaze_surrogate* s, const Samples& S, int* status, cudaStream_t st);
 
 }  // namespace sg
 }  // namespace kz

@@ -127,6 +127,7 @@ _SIGNATURES = {
     "kaze_surrogate_train_step": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_f),
                                        ctypes.POINTER(_vp), _i, _i, _i, _i, _f, ctypes.POINTER(ctypes.c_double)]),
     "kaze_surrogate_steps_taken": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "kaze_surrogate_sync": (_i, [_vp]),
     "kaze_surrogate_save": (_i, [_vp, ctypes.c_char_p]),
     "kaze_surrogate_load": (_i, [_vp, ctypes.c_char_p]),
     "kaze_surrogate_last_launch_count": (_i, [_vp]),
@@ -637,6 +638,7 @@ SURROGATE_MAX_SAMPLES = 64
 SURROGATE_TRAIN = 1
 SURROGATE_FUSED = 0
 SURROGATE_LAYERED = 1
+SURROGATE_FUSED_SYNC = 2
 
 
 def _planes(x, name):
@@ -778,6 +780,10 @@ class Surrogate:
             raise KazeError(ERR_INVALID_ARG, f"expected {SURROGATE_PARAMS} parameters")
         self._ck(self._L.kaze_surrogate_set_params(self._s, p.ctypes.data_as(ctypes.POINTER(_f)), p.size),
                  "kaze_surrogate_set_params")
+
+    def sync(self):
+        """Waits for the surrogate's stream; raises on a device-side timeout."""
+        self._ck(self._L.kaze_surrogate_sync(self._s), "kaze_surrogate_sync")
 
     def steps_taken(self):
         n = ctypes.c_longlong(0)
