@@ -143,3 +143,51 @@ def evaluate(surrogate, images, octaves=4, sublevels=4, batch_reps=5):
         "evolution_ms_aos": float(np.mean(t_aos)), "evolution_ms_surrogate": float(np.mean(t_sg)),
         "batched_step_ms_surrogate": best_sg, "batched_step_ms_aos": best_aos,
     }
+
+
+def time_step(w, h, n, path="fused", reps=10, warmup=3, checkpoint=None, seed=0):
+    """Device time of one surrogate step over n seeded w x h planes (one
+    launch for the fused paths), CUDA events on the surrogate's stream;
+    returns ms per step and the rate in logical TFLOP/s of the 5-32-32-32-1
+    network (2 x 9 x 2208 FLOP per pixel)."""
+    import torch
+    from . import kaze
+    paths = {"fused": kaze.SURROGATE_FUSED, "fused_sync": kaze.SURROGATE_FUSED_SYNC,
+             "layered": kaze.SURROGATE_LAYERED}
+    s = kaze.Surrogate(max_w=w, max_h=h, max_samples=n, seed=seed)
+    if checkpoint:
+        s.load(checkpoint)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    L = torch.rand(n, h, w, generator=gen).cuda()
+    g = torch.rand(n, h, w, generator=gen).cuda()
+    out = torch.empty_like(L)
+    tau = [4.0] * n
+    for _ in range(warmup):
+        s.step(L, g, tau, out, path=paths[path])
+    s.sync()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    for _ in range(reps):
+        s.step(L, g, tau, out, path=paths[path])
+    e1.record(s.stream)
+    s.sync()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    s.close()
+    flops = 2.0 * 9 * (5 * 32 + 32 * 32 + 32 * 32 + 32 * 1) * w * h * n
+    return {"path": path, "images": n, "size": [w, h], "ms": ms, "tflops": flops / ms * 1e-9}
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="Time one surrogate step on seeded planes.")
+    ap.add_argument("--size", type=int, nargs=2, default=[1920, 1200], metavar=("W", "H"))
+    ap.add_argument("--images", type=int, default=1)
+    ap.add_argument("--path", choices=["fused", "fused_sync", "layered"], default="fused")
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--checkpoint", default=None)
+    a = ap.parse_args()
+    print(json.dumps(time_step(a.size[0], a.size[1], a.images, a.path, a.reps, a.warmup, a.checkpoint)))
