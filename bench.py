@@ -167,7 +167,7 @@ KIND_SOURCES = {
     "percentile": ["k_filters.cu"], "conductance": ["k_filters.cu"],
     "aos_rows": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
     "aos_cols": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
-    "doh": ["k_detector.cu"], "extrema": ["k_detector.cu"],
+    "doh": ["k_detector.cu"], "extrema": ["k_detector.cu"], "describe": ["k_describe.cu"],
 }
 
 
@@ -366,6 +366,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = kernels[dom]["algorithmic_gbs"]
     traffic = ncu_traffic(dom)
 
+    describe = run_describe(args, k, torch, stream, flush, k.detect(x), slowest, barrier)
     batched = None if args.no_batch else run_batched(args, kaze, synth, torch, stream, world, rank,
                                                         slowest, barrier)
     surrogate = None if args.no_surrogate else run_surrogate(args, kaze, synth, torch, rank)
@@ -403,6 +404,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes},
         "kernels": kernels,
+        "describe": describe,
         "batched": batched,
         "surrogate": surrogate,
         "cpu_baseline": cpu,
@@ -412,6 +414,34 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
     k.close()
     return 0
+
+
+def run_describe(args, k, torch, stream, flush, kp, max_over_ranks, barrier):
+    """Orientation + 64-D M-SURF descriptor (Sec. II-C) of the workload
+    image's keypoints on its device-resident levels: one launch per step, the
+    keypoints already on the device, L2 flushed before every step."""
+    n = len(kp)
+    if n == 0:
+        return {"keypoints": 0}
+    d_kp = k.keypoints_to_device(kp)
+    d_desc = torch.empty((n, 64), device="cuda")
+    for _ in range(args.warmup):
+        k.describe_device(d_kp, d_desc, n)
+    reps = max(3, min(args.steps, 50))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    barrier()
+    with torch.cuda.stream(stream):
+        for i in range(reps):
+            flush.zero_()
+            starts[i].record(stream)
+            k.describe_device(d_kp, d_desc, n)
+            ends[i].record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / reps)
+    return {"keypoints": n, "ms_per_step": ms, "us_per_keypoint": ms * 1e3 / n,
+            "keypoints_per_s": n / (ms * 1e-3), "launches_per_step": k.last_launch_count(),
+            "l2": "flushed before every step"}
 
 
 def run_batched(args, kaze, synth, torch, stream, world, rank, max_over_ranks, barrier):

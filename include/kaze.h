@@ -94,8 +94,9 @@ void kaze_default_options(kaze_options* opt);
  * each row and column is solved by 32 chunks whose coefficients must fit in
  * registers and shared memory).
  * Allocates all device buffers up front (about (2N + 3) * max_w * max_h * 4
- * bytes).  cuda_stream: the cudaStream_t all work goes to.  On error *out is
- * NULL.  Errors: INVALID_ARG (bad options or sizes), OOM, CUDA. */
+ * bytes, plus 336 bytes per keypoint of max_keypoints).  cuda_stream: the
+ * cudaStream_t all work goes to.  On error *out is NULL.  Errors:
+ * INVALID_ARG (bad options or sizes), OOM, CUDA. */
 kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h,
                         void* cuda_stream, kaze_handle** out);
 
@@ -145,6 +146,42 @@ kaze_status kaze_detect(kaze_handle* h, const float* d_img, int w, int h_, int p
  * host buffer should be page-locked (e.g. torch pinned memory). */
 kaze_status kaze_detect_host(kaze_handle* h, const float* h_img, int w, int h_, int pitch_elems,
                              kaze_keypoint* h_out, int capacity, int* count);
+
+/* ---- description (Sec. II-C) --------------------------------------------- *
+ * Dominant orientation and 64-D M-SURF descriptor of keypoints on the levels
+ * of the last kaze_build_scale_space (any level of the stack, all in one
+ * launch).  Per keypoint: first derivatives of its level L_i by the step-s_i
+ * Scharr pair of the detector, sampled bilinearly (taps clamped into the
+ * image); the orientation is the angle of the longest response sum over pi/3
+ * windows (72 five-degree sectors) of 109 samples within 6 sigma_i, weighted
+ * by a Gaussian of std 2.5 sigma_i; the descriptor sums (r_x', r_y', |r_x'|,
+ * |r_y'|) in the rotated frame over 4 x 4 subregions of 9 x 9 samples spaced
+ * sigma_i (centres 5 sigma_i apart, 24 sigma_i window) with Gaussian weights
+ * of std 2.5 sigma_i per subregion and 1.5 grid units over the 4 x 4 mask;
+ * entry 4 (4 q + p) + c holds component c of subregion (p, q) (p along the
+ * orientation, q across it) and the 64 entries have unit Euclidean norm.
+ * upright != 0 skips the orientation (angle 0).  The keypoint's x, y (sub-
+ * pixel, full resolution) and level are read; its sigma field is not (the
+ * level's sigma_i is used); angle receives the orientation in radians, in
+ * [0, 2 pi). */
+
+/* Host arrays: kps (n keypoints, angle written back) and desc (n x 64
+ * floats, row k for kps[k]).  Synchronises.  Errors: INVALID_ARG (NULL
+ * arrays with n > 0, a level outside 0..N-1, a non-finite position), STATE
+ * (no build yet), CAPACITY (n > max_keypoints), CUDA. */
+kaze_status kaze_describe(kaze_handle* h, kaze_keypoint* kps, int n, float* desc, int upright);
+
+/* Device arrays d_kps (n keypoints, angle written back) and d_desc (n x 64
+ * floats); asynchronous on the handle's stream, no size limit beyond the
+ * caller's buffers.  A keypoint whose level is outside 0..N-1 gets a zero
+ * descriptor and angle 0. */
+kaze_status kaze_describe_device(kaze_handle* h, kaze_keypoint* d_kps, int n, float* d_desc, int upright);
+
+/* Description on one caller-supplied level image d_L (w x h_, pitch) of scale
+ * sigma: every keypoint is taken to lie on it (its level is ignored).  Host
+ * kps / desc as kaze_describe; synchronises. */
+kaze_status kaze_op_describe(kaze_handle* h, const float* d_L, int pitch, int w, int h_, float sigma,
+                             kaze_keypoint* kps, int n, float* desc, int upright);
 
 /* ---- single steps, for testing each kernel on given inputs -------------- *
  * These run one step of the method on caller-owned device buffers on the

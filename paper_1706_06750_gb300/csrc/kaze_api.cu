@@ -25,11 +25,11 @@ namespace {
 // Kernel kinds, in pipeline order, for launch counting and profiling.
 enum KernelKind {
     KK_PRESMOOTH = 0, KK_GRAD_MAX, KK_GRAD_HIST, KK_PERCENTILE, KK_SET_SCALAR,
-    KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_SURROGATE, KK_COUNT
+    KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_SURROGATE, KK_DESCRIBE, KK_COUNT
 };
 const char* const kKindNames[KK_COUNT] = {
     "presmooth", "grad_max", "grad_hist", "percentile", "set_scalar",
-    "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate"};
+    "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate", "describe"};
 }  // namespace
 
 struct kaze_handle {
@@ -55,6 +55,8 @@ struct kaze_handle {
     unsigned int* d_count = nullptr;
     int* d_status = nullptr;         // bit 0: a bounded device wait ran out
     kaze_keypoint* d_kp = nullptr;
+    kaze_keypoint* d_dkp = nullptr;  // keypoints uploaded for description
+    float* d_desc = nullptr;         // their descriptors, max_keypoints x 64
     unsigned int* h_count = nullptr;  // pinned
     int* h_status = nullptr;          // pinned
 
@@ -479,6 +481,10 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
             ce = kz::configure_detector_kernels();
             what = "configure_detector_kernels";
         }
+        if (ce == cudaSuccess) {
+            ce = kz::configure_describe_kernels();
+            what = "configure_describe_kernels";
+        }
         if (ce != cudaSuccess) {
             delete h;
             return create_fail(KAZE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(ce) + " " +
@@ -500,6 +506,8 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     const size_t off_cnt = bytes;    bytes += al(sizeof(unsigned int));
     const size_t off_status = bytes; bytes += al(sizeof(int));
     const size_t off_kp = bytes;     bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
+    const size_t off_dkp = bytes;    bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
+    const size_t off_desc = bytes;   bytes += al(sizeof(float) * 64 * (size_t)o.max_keypoints);
     cudaError_t e = cudaMalloc(&h->arena, bytes);
     if (e != cudaSuccess) {
         delete h;
@@ -518,6 +526,8 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     h->d_count = (unsigned int*)(a + off_cnt);
     h->d_status = (int*)(a + off_status);
     h->d_kp = (kaze_keypoint*)(a + off_kp);
+    h->d_dkp = (kaze_keypoint*)(a + off_dkp);
+    h->d_desc = (float*)(a + off_desc);
     e = cudaMallocHost(&h->h_count, 2 * sizeof(unsigned int));
     if (e != cudaSuccess) {
         cudaFree(h->arena);
@@ -623,6 +633,90 @@ KAZE_API kaze_status kaze_detect_host(kaze_handle* h, const float* h_img, int w,
                                 sizeof(float) * w, hh, cudaMemcpyHostToDevice, h->stream));
     KZ_CHECK(run_detect_graph(h, h->staging, w, hh, sp));
     return collect_keypoints(h, h_out, capacity, count);
+}
+
+// ---- description (Sec. II-C) -------------------------------------------------
+
+namespace {
+
+kz::DescTable desc_table(const kaze_handle* h)
+{
+    kz::DescTable t;
+    std::memset(&t, 0, sizeof(t));
+    t.n = h->N;
+    t.single = 0;
+    for (int i = 0; i < h->N; ++i) {
+        t.sigma[i] = (float)h->sigma[i];
+        t.step[i] = h->tab.step[i];
+    }
+    return t;
+}
+
+kaze_status check_host_keypoints(kaze_handle* h, const kaze_keypoint* kps, int n, bool need_level)
+{
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(kps[i].x) || !std::isfinite(kps[i].y))
+            return fail(h, KAZE_ERR_INVALID_ARG, "keypoint position is not finite");
+        if (need_level && (kps[i].level < 0 || kps[i].level >= h->N))
+            return fail(h, KAZE_ERR_INVALID_ARG, "keypoint level out of range");
+    }
+    return KAZE_OK;
+}
+
+// Upload, describe, download; synchronises.
+kaze_status describe_host(kaze_handle* h, const float* levels, long long plane, int pitch, int w, int hh,
+                          const kz::DescTable& tab, kaze_keypoint* kps, int n, float* desc, int upright)
+{
+    h->launches = 0;
+    if (n == 0) return KAZE_OK;
+    KZ_TRY(h, cudaMemcpyAsync(h->d_dkp, kps, sizeof(kaze_keypoint) * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    KZ_LAUNCH(h, KK_DESCRIBE, kz::launch_describe(levels, plane, pitch, w, hh, tab, h->d_dkp, n, h->d_desc, upright,
+                                                  h->stream));
+    KZ_TRY(h, cudaMemcpyAsync(desc, h->d_desc, sizeof(float) * 64 * (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+    KZ_TRY(h, cudaMemcpyAsync(kps, h->d_dkp, sizeof(kaze_keypoint) * (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+    KZ_TRY(h, cudaStreamSynchronize(h->stream));
+    return KAZE_OK;
+}
+
+}  // namespace
+
+KAZE_API kaze_status kaze_describe(kaze_handle* h, kaze_keypoint* kps, int n, float* desc, int upright)
+{
+    if (!h || n < 0 || (n > 0 && (!kps || !desc))) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    if (!h->built) return fail(h, KAZE_ERR_STATE, "no scale space built yet");
+    if (n > h->opt.max_keypoints) return fail(h, KAZE_ERR_CAPACITY, "more keypoints than max_keypoints");
+    KZ_CHECK(check_host_keypoints(h, kps, n, true));
+    return describe_host(h, h->levels, h->cur_plane, h->cur_pitch, h->cur_w, h->cur_h, desc_table(h), kps, n, desc,
+                         upright);
+}
+
+KAZE_API kaze_status kaze_describe_device(kaze_handle* h, kaze_keypoint* d_kps, int n, float* d_desc, int upright)
+{
+    if (!h || n < 0 || (n > 0 && (!d_kps || !d_desc))) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    if (!h->built) return fail(h, KAZE_ERR_STATE, "no scale space built yet");
+    h->launches = 0;
+    if (n == 0) return KAZE_OK;
+    KZ_LAUNCH(h, KK_DESCRIBE, kz::launch_describe(h->levels, h->cur_plane, h->cur_pitch, h->cur_w, h->cur_h,
+                                                  desc_table(h), d_kps, n, d_desc, upright, h->stream));
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_op_describe(kaze_handle* h, const float* d_L, int pitch, int w, int hh, float sigma,
+                                      kaze_keypoint* kps, int n, float* desc, int upright)
+{
+    if (!h || !d_L || n < 0 || (n > 0 && (!kps || !desc))) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
+    if (!(sigma > 0.f) || !std::isfinite(sigma) || sigma > 1e4f) return fail(h, KAZE_ERR_INVALID_ARG, "bad sigma");
+    if (n > h->opt.max_keypoints) return fail(h, KAZE_ERR_CAPACITY, "more keypoints than max_keypoints");
+    KZ_CHECK(check_host_keypoints(h, kps, n, false));
+    kz::DescTable t;
+    std::memset(&t, 0, sizeof(t));
+    t.n = 1;
+    t.single = 1;
+    t.sigma[0] = sigma;
+    t.step[0] = step_of(sigma);
+    return describe_host(h, d_L, 0, pitch, w, hh, t, kps, n, desc, upright);
 }
 
 // ---- single steps ----------------------------------------------------------

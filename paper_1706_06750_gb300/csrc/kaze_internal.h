@@ -30,6 +30,15 @@ struct LevelTable {
     int sublevels;               // S (octave = i / S, sublevel = i % S)
 };
 
+// Per-level constants of keypoint description (Sec. II-C), passed by value.
+// single != 0: one caller-supplied level (entry 0) serves every keypoint.
+struct DescTable {
+    int n;
+    int single;
+    float sigma[kMaxLevels];
+    int step[kMaxLevels];
+};
+
 // Half-sample symmetric reflection of i into [0, n).
 __host__ __device__ __forceinline__ int reflect_index(int i, int n)
 {
@@ -133,6 +142,15 @@ cudaError_t launch_extrema(const float* D, int pitch, long long plane_stride, in
                            int n, const LevelTable& tab, float dthreshold, float edge_r,
                            kaze_keypoint* d_kp, int cap, unsigned int* d_count,
                            cudaStream_t st);
+
+// Orientation and 64-D M-SURF descriptor of n device keypoints (angle
+// written back into d_kps, descriptors to d_desc, n x 64); keypoint k lies on
+// level kps[k].level of the stack (or on the single level).  Tables are
+// uploaded by configure_describe_kernels.
+cudaError_t configure_describe_kernels();
+cudaError_t launch_describe(const float* levels, long long plane_stride, int pitch, int w, int h,
+                            const DescTable& tab, kaze_keypoint* d_kps, int n, float* d_desc, int upright,
+                            cudaStream_t st);
 
 // Handle runtime helpers used by the batch API (kaze_api.cu).
 kaze_status handle_enqueue_into(kaze_handle* h, const float* d_img, int w, int hh, int pitch, float* levels,

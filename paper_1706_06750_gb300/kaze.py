@@ -138,6 +138,9 @@ _SIGNATURES = {
     "kaze_kernel_name": (ctypes.c_char_p, [_i]),
     "kaze_last_launch_count": (_i, [_vp]),
     "kaze_profile": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)]),
+    "kaze_describe": (_i, [_vp, _vp, _i, _vp, _i]),
+    "kaze_describe_device": (_i, [_vp, _vp, _i, _vp, _i]),
+    "kaze_op_describe": (_i, [_vp, _vp, _i, _i, _i, _f, _vp, _i, _vp, _i]),
     "kaze_status_string": (ctypes.c_char_p, [_i]),
     "kaze_last_error": (ctypes.c_char_p, [_vp]),
     "kaze_destroy": (None, [_vp]),
@@ -244,6 +247,13 @@ class Kaze:
             raise KazeError(st, f"{what}: {self._L.kaze_status_string(st).decode()}: {msg}")
         return st
 
+    def _raise_all(self, st, what):
+        """Like _ck, but a capacity error raises too (nothing was done)."""
+        if st == ERR_CAPACITY:
+            msg = self._L.kaze_last_error(self._h).decode()
+            raise KazeError(st, f"{what}: {self._L.kaze_status_string(st).decode()}: {msg}")
+        return self._ck(st, what)
+
     def close(self):
         if getattr(self, "_h", None):
             self._L.kaze_destroy(self._h)
@@ -306,6 +316,12 @@ class Kaze:
     def levels(self):
         import torch
         return torch.stack([self.level(i) for i in range(self.n_levels)])
+
+    def level_sigma(self, i):
+        """sigma_i of level i as the library holds it (Eq. 6, FP32)."""
+        o = self.options
+        oc, sub = divmod(int(i), o.sublevels)
+        return float(np.float32(float(np.float32(o.sigma0)) * 2.0 ** (oc + sub / o.sublevels)))
 
     def level_time(self, i):
         t = _f()
@@ -383,6 +399,65 @@ class Kaze:
         self.last_status = st
         self.last_count = n.value
         return _sorted_keypoints(buf, min(n.value, cap))
+
+    # -- description (Sec. II-C) --
+    def describe(self, keypoints, upright=False):
+        """Orientation and 64-D M-SURF descriptor of keypoints (a KEYPOINT_DTYPE
+        array, e.g. from detect) on the levels of the last build.  Returns a
+        copy of the keypoints with their angle set and the [n, 64] float32
+        descriptors."""
+        kp = np.ascontiguousarray(np.asarray(keypoints, dtype=KEYPOINT_DTYPE)).copy()
+        n = len(kp)
+        desc = np.zeros((n, 64), dtype=np.float32)
+        self._begin()
+        st = self._L.kaze_describe(self._h, _vp(kp.ctypes.data if n else None), n,
+                                   _vp(desc.ctypes.data if n else None), int(bool(upright)))
+        self._end()
+        self._raise_all(st, "kaze_describe")
+        return kp, desc
+
+    def describe_device(self, d_kps, d_desc, n, upright=False):
+        """kaze_describe_device on device buffers: d_kps a CUDA tensor holding
+        n keypoint records (see keypoints_to_device), d_desc a [n, 64] float32
+        CUDA tensor.  Asynchronous on the handle's stream."""
+        self._begin()
+        self._ck(self._L.kaze_describe_device(self._h, _vp(d_kps.data_ptr()), int(n), _vp(d_desc.data_ptr()),
+                                              int(bool(upright))), "kaze_describe_device")
+        self._end()
+
+    @staticmethod
+    def keypoints_to_device(keypoints):
+        """A CUDA uint8 tensor holding the keypoint records byte for byte."""
+        import torch
+        kp = np.ascontiguousarray(np.asarray(keypoints, dtype=KEYPOINT_DTYPE))
+        return torch.from_numpy(kp.view(np.uint8).copy()).cuda()
+
+    @staticmethod
+    def keypoints_from_device(t, n):
+        return np.frombuffer(t[: n * KEYPOINT_DTYPE.itemsize].cpu().numpy().tobytes(), dtype=KEYPOINT_DTYPE,
+                             count=n).copy()
+
+    def op_describe(self, L, sigma, points, upright=False):
+        """Description on one given level image L (2-D float32 CUDA tensor) of
+        scale sigma at points: a KEYPOINT_DTYPE array or a sequence of (x, y).
+        Returns (angles [n], descriptors [n, 64])."""
+        w, h, pitch = _check_image(L)
+        if isinstance(points, np.ndarray) and points.dtype == KEYPOINT_DTYPE:
+            kp = np.ascontiguousarray(points).copy()
+        else:
+            pts = list(points)
+            kp = np.zeros(len(pts), dtype=KEYPOINT_DTYPE)
+            for i, (x, y) in enumerate(pts):
+                kp[i]["x"], kp[i]["y"] = x, y
+        n = len(kp)
+        desc = np.zeros((n, 64), dtype=np.float32)
+        self._begin()
+        st = self._L.kaze_op_describe(self._h, _vp(L.data_ptr()), pitch, w, h, float(sigma),
+                                      _vp(kp.ctypes.data if n else None), n,
+                                      _vp(desc.ctypes.data if n else None), int(bool(upright)))
+        self._end()
+        self._raise_all(st, "kaze_op_describe")
+        return kp["angle"].astype(np.float64), desc
 
     # -- instrumentation --
     def set_surrogate(self, surrogate):
