@@ -322,28 +322,32 @@ def test_full_size_1920x1200_against_oracle(kz):
 
 
 def test_full_size_4096x3072_sampled_steps(kz):
-    """4096x3072 (12.6 Mpx): GPU run end to end; the oracle recomputes two
-    AOS steps from the GPU's own previous level and the response of one
-    level, and the mean / range invariants hold at every level."""
+    """4096x3072 (12.6 Mpx): the GPU pipeline end to end (every level keeps
+    the mean of L_0, keypoints are found), and single steps at full size on
+    inputs the oracle makes itself: the oracle's presmoothed image and its
+    conductance feed two AOS steps (the step sizes of levels 1 and 15) and
+    the response of level 9 on both sides."""
     img = synth.workload_image("4096x3072")
     h, w = img.shape
+    sig, t = oracle.scale_table(4, 4, 1.6)
+    L0 = oracle.gaussian(img.astype(np.float64), 1.6).astype(np.float32)
+    kref = oracle.contrast_k(L0.astype(np.float64))[0]
+    g = oracle.conductance(L0.astype(np.float64), kref, 1.0, oracle.G2).astype(np.float32)
     with kz.Kaze(w, h, octaves=4, sublevels=4) as k:
         x = dev(img)
         k.build_scale_space(x)
-        kval = k.contrast()
         k.detector_response()
         kp = k.find_extrema()
-        sig, t = oracle.scale_table(4, 4, 1.6)
         means = [float(k.level(i, copy=False).double().mean()) for i in range(16)]
+        L0d, gd = dev(L0), dev(g)
+        ux, Ln, D = torch.empty_like(L0d), torch.empty_like(L0d), torch.empty_like(L0d)
         for i in (1, 15):
-            Lp = host(k.level(i - 1))
-            Li = host(k.level(i))
-            g = oracle.conductance(Lp, float(kval), 1.0, oracle.G2)
-            _, _, ref = oracle.aos_step(Lp, g, float(np.float32(t[i] - t[i - 1])))
-            assert np.max(np.abs(Li - ref)) <= SCALE_TOL
-        L9 = host(k.level(9))
-        D9 = host(k.response(9))
-        ref = oracle.doh(L9, sig[9], 2)
-        assert np.max(np.abs(D9 - ref)) <= DOH_REL_TOL * np.max(np.abs(ref))
+            tau = float(np.float32(t[i] - t[i - 1]))
+            k.op_aos_step(L0d, gd, ux, Ln, tau)
+            _, _, ref = oracle.aos_step(L0.astype(np.float64), g.astype(np.float64), tau)
+            assert np.max(np.abs(host(Ln) - ref)) <= SCALE_TOL
+        k.op_doh(L0d, D, float(np.float32(sig[9])), 2)
+        ref = oracle.doh(L0.astype(np.float64), float(np.float32(sig[9])), 2)
+        assert np.max(np.abs(host(D) - ref)) <= DOH_REL_TOL * np.max(np.abs(ref))
     assert max(abs(m - means[0]) for m in means) < 1e-5
     assert len(kp) >= 100
