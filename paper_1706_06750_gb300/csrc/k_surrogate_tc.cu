@@ -25,10 +25,10 @@
 // weights); an instruction of N = 96 costs little more than one of N = 32,
 // so a layer takes a third of the instructions of a tap-by-tap GEMM.
 //
-// Warp roles: warp 8 allocates 512 columns of tensor memory and one of its
+// Warp roles: warp 16 allocates 512 columns of tensor memory and one of its
 // threads issues every MMA into a ring of five 96-column slots, committing
-// each M tile to the slot's "full" barrier; warps 0-7 (two groups of four,
-// alternating tiles, each warp its quarter of the 128 lanes) read a full
+// each M tile to the slot's "full" barrier; warps 0-15 (four groups of four
+// taking every fourth tile, each warp its quarter of the 128 lanes) read a full
 // slot (tcgen05.ld), release it on its "empty" barrier, add bias and ReLU,
 // zero the padding outside the image and write the next layer's operand (or
 // L_next).  A layer's MMAs start once every epilogue warp has finished the
@@ -50,14 +50,15 @@ constexpr int TC_F = TC_T + 8;            // frame edge (32)
 constexpr int TC_FP = TC_F * TC_F;        // frame pixels (1024)
 constexpr int TC_FS = 64;                 // front slack pixels (operands start up to 32 before)
 constexpr int TC_BP = TC_FS + TC_FP + 192;  // pixels per channel group incl. slack (1280)
-constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_EPI_WARPS = 16;           // four groups of four
+constexpr int TC_GROUPS = TC_EPI_WARPS / 4;
 constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + 1);
 constexpr int TC_SLOTS = 5;               // tensor-memory ring
 constexpr int TC_SLOT_COLS = 96;
 constexpr int TC_TMEM_COLS = 512;
 constexpr uint32_t TC_LBO_ACT = TC_BP * 16;   // bytes between channel groups of an activation buffer
 static_assert(TC_SLOTS * TC_SLOT_COLS <= TC_TMEM_COLS, "ring fits the allocation");
-static_assert(TC_SLOTS % 2 == 1, "slot reuse alternates the epilogue groups");
+static_assert(TC_SLOTS > TC_GROUPS, "every group can hold a slot while the next tile fills");
 
 // weight buffers: per kernel row ky, [CIN/8][N][8] BF16 with N = 3 C
 constexpr int W1_BYTES = 3 * (kC0 / 8) * 96 * 16;
@@ -135,6 +136,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r)
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+
+// bar_wait for a whole warp: one lane polls, then every lane observes the
+// completed phase itself (acquire for each thread).  Same result in all lanes.
+__device__ __forceinline__ bool warp_bar_wait(uint64_t* bar, uint32_t parity, long long limit, int lane)
+{
+    bool ok = true;
+    if (lane == 0) ok = bar_wait(bar, parity, limit);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (ok) ok = bar_wait(bar, parity, limit);
+    return __all_sync(0xffffffffu, ok);
 }
 
 __device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr)
@@ -329,7 +341,7 @@ k_surrogate_tc(const __nv_bfloat16* __restrict__ wpad, const float* __restrict__
         __syncwarp();
     } else {
         // ---- epilogue warps ----
-        const int group = warp >> 2;
+        const int group = warp >> 2;  // handles the M tiles T = group (mod TC_GROUPS)
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lane quarter
         uint32_t T = 0;
         int frame = 0;
@@ -342,9 +354,9 @@ k_surrogate_tc(const __nv_bfloat16* __restrict__ wpad, const float* __restrict__
                 const int tiles = tiles_of(l);
                 const int p0 = l * TC_F;
                 for (int m = 0; m < tiles; ++m, ++T) {
-                    if ((int)(T & 1u) != group) continue;
+                    if ((int)(T % TC_GROUPS) != group) continue;
                     const uint32_t slot = T % TC_SLOTS, use = T / TC_SLOTS;
-                    if (!bar_wait(&bars.full[slot], use & 1u, spin_limit)) {
+                    if (!warp_bar_wait(&bars.full[slot], use & 1u, spin_limit, lane)) {
                         if (lane == 0) atomicOr(status, 1);
                         s_fail = 1;
                         break;
@@ -409,7 +421,7 @@ k_surrogate_tc(const __nv_bfloat16* __restrict__ wpad, const float* __restrict__
                 if (l == 3 && !s_fail) {
                     // layer 3 read buffer A: once every warp is past it, stage the
                     // next frame's input there while layer 4 runs on buffer B
-                    if (!bar_wait(&bars.layer, (uint32_t)(4 * frame + 2) & 1u, spin_limit)) {
+                    if (!warp_bar_wait(&bars.layer, (uint32_t)(4 * frame + 2) & 1u, spin_limit, lane)) {
                         if (lane == 0) atomicOr(status, 1);
                         s_fail = 1;
                         break;
