@@ -34,6 +34,8 @@ G1 = 1
 G2 = 2
 DOH_SIGMA4 = 0
 DOH_PAPER_LITERAL = 1
+SCHEME_AOS = 0
+SCHEME_FED = 1
 
 
 class Options(ctypes.Structure):
@@ -51,14 +53,16 @@ class Options(ctypes.Structure):
         ("edge_r", ctypes.c_double),
         ("doh_norm", ctypes.c_int),
         ("k_override", ctypes.c_double),
+        ("scheme", ctypes.c_int),
+        ("fed_tau_max", ctypes.c_double),
     ]
 
     @classmethod
     def make(cls, octaves=4, sublevels=4, sigma0=1.6, sigma_d=1.0,
              k_percentile=0.7, nbins=300, diffusivity=G2, dthreshold=0.001,
-             edge_r=10.0, doh_norm=DOH_SIGMA4, k_override=0.0):
+             edge_r=10.0, doh_norm=DOH_SIGMA4, k_override=0.0, scheme=0, fed_tau_max=0.25):
         return cls(octaves, sublevels, sigma0, sigma_d, k_percentile, nbins,
-                   diffusivity, dthreshold, edge_r, doh_norm, k_override)
+                   diffusivity, dthreshold, edge_r, doh_norm, k_override, scheme, fed_tau_max)
 
 
 class Keypoint(ctypes.Structure):
@@ -120,6 +124,9 @@ def _load():
         "ko_conductance": (None, [dp, i, i, d, d, i, dp]),
         "ko_thomas": (None, [i, dp, dp, dp, dp, dp]),
         "ko_aos_step": (None, [dp, dp, i, i, d, dp, dp, dp]),
+        "ko_fed_tau": (i, [d, d, dp, i]),
+        "ko_fed_step": (None, [dp, dp, i, i, d, dp]),
+        "ko_fed_evolve": (i, [dp, dp, i, i, d, d, dp]),
         "ko_build_scale_space": (i, [dp, i, i, ctypes.POINTER(Options), dp, dp]),
         "ko_step_size": (i, [d]),
         "ko_hessian": (None, [dp, i, i, i, dp, dp, dp]),
@@ -226,6 +233,34 @@ def aos_step(Lprev, g, tau: float):
     ln, lnp = _out((h, w))
     _load().ko_aos_step(lp, gp, w, h, tau, uxp, uyp, lnp)
     return ux, uy, ln
+
+
+def fed_tau(dt: float, tau_max: float = 0.25) -> np.ndarray:
+    """Step sizes of one FED cycle reaching stopping time dt (Eq. 5)."""
+    n = _load().ko_fed_tau(dt, tau_max, None, 0)
+    t, tp = _out((max(n, 1),))
+    _load().ko_fed_tau(dt, tau_max, tp, n)
+    return t[:n]
+
+
+def fed_step(L, g, tau: float) -> np.ndarray:
+    """One explicit step with fixed conductance (flux form, no flux through the border)."""
+    L, lp = _c(L)
+    g, gp = _c(g)
+    h, w = L.shape
+    out, op = _out((h, w))
+    _load().ko_fed_step(lp, gp, w, h, tau, op)
+    return out
+
+
+def fed_evolve(L, g, dt: float, tau_max: float = 0.25) -> np.ndarray:
+    """One FED cycle from L to stopping time dt with fixed conductance g."""
+    L, lp = _c(L)
+    g, gp = _c(g)
+    h, w = L.shape
+    out, op = _out((h, w))
+    _load().ko_fed_evolve(lp, gp, w, h, dt, tau_max, op)
+    return out
 
 
 def build_scale_space(img, opt: Options | None = None):

@@ -264,8 +264,68 @@ void ko_aos_step(const double* Lprev, const double* g, int W, int H,
     free(vx); free(vy); free(gl); free(dl); free(vl);
 }
 
+/* Stopping time of one FED cycle of n steps with limit tau_max. */
+static double fed_cycle_time(int n, double tau_max)
+{
+    return tau_max * ((double)n * n + n) / 3.0;
+}
+
+/* Eq. 5 with readings F1-F3 (see the header). */
+int ko_fed_tau(double dt, double tau_max, double* tau, int cap)
+{
+    if (!(dt > 0.0) || !(tau_max > 0.0)) return 0;
+    int n = (int)ceil(sqrt(3.0 * dt / tau_max + 0.25) - 0.5);
+    if (n < 1) n = 1;
+    while (fed_cycle_time(n, tau_max) < dt) ++n;
+    while (n > 1 && fed_cycle_time(n - 1, tau_max) >= dt) --n;
+    const double scale = dt / fed_cycle_time(n, tau_max);
+    const double pi = 3.14159265358979323846;
+    for (int j = 0; j < n && j < cap; ++j) {
+        const double c = cos(pi * (2.0 * j + 1.0) / (4.0 * n + 2.0));
+        tau[j] = scale * tau_max / (2.0 * c * c);
+    }
+    return n;
+}
+
+/* F4: explicit step of div(g grad L) in the flux form of the AOS operator. */
+void ko_fed_step(const double* L, const double* g, int W, int H, double tau, double* out)
+{
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            double flux = 0.0;
+            if (x > 0) flux += 0.5 * (g[p] + g[p - 1]) * (L[p - 1] - L[p]);
+            if (x < W - 1) flux += 0.5 * (g[p] + g[p + 1]) * (L[p + 1] - L[p]);
+            if (y > 0) flux += 0.5 * (g[p] + g[p - W]) * (L[p - W] - L[p]);
+            if (y < H - 1) flux += 0.5 * (g[p] + g[p + W]) * (L[p + W] - L[p]);
+            out[p] = L[p] + tau * flux;
+        }
+}
+
+int ko_fed_evolve(const double* L, const double* g, int W, int H, double dt, double tau_max,
+                  double* out)
+{
+    size_t P = (size_t)W * H;
+    int n = ko_fed_tau(dt, tau_max, NULL, 0);
+    double* tau = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    ko_fed_tau(dt, tau_max, tau, n);
+    double* a = (double*)malloc(sizeof(double) * P);
+    double* b = (double*)malloc(sizeof(double) * P);
+    memcpy(a, L, sizeof(double) * P);
+    for (int j = 0; j < n; ++j) {
+        ko_fed_step(a, g, W, H, tau[j], b);
+        double* t = a;
+        a = b;
+        b = t;
+    }
+    memcpy(out, a, sizeof(double) * P);
+    free(a); free(b); free(tau);
+    return n;
+}
+
 /* Sec. II-A / III-1: presmoothing with sigma0, k from the base image, then
- * one AOS step per level with tau_i = t_i - t_{i-1} (Eq. 7). */
+ * one AOS step (or one FED cycle) per level with tau_i = t_i - t_{i-1}
+ * (Eq. 7). */
 int ko_build_scale_space(const double* img, int W, int H, const ko_options* opt,
                          double* levels, double* k_used)
 {
@@ -288,7 +348,10 @@ int ko_build_scale_space(const double* img, int W, int H, const ko_options* opt,
         const double* Lp = levels + (size_t)(i - 1) * P;
         double* Li = levels + (size_t)i * P;
         ko_conductance(Lp, W, H, opt->sigma_d, k, opt->diffusivity, g);
-        ko_aos_step(Lp, g, W, H, t[i] - t[i - 1], NULL, NULL, Li);
+        if (opt->scheme == KO_SCHEME_FED)
+            ko_fed_evolve(Lp, g, W, H, t[i] - t[i - 1], opt->fed_tau_max, Li);
+        else
+            ko_aos_step(Lp, g, W, H, t[i] - t[i - 1], NULL, NULL, Li);
     }
     free(sigma); free(t); free(g);
     return 0;

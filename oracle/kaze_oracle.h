@@ -24,6 +24,10 @@ extern "C" {
 #define KO_G1 1   /* exp(-|grad|^2 / k^2) */
 #define KO_G2 2   /* 1 / (1 + |grad|^2 / k^2)  (default) */
 
+/* Evolution scheme of each level (Sec. II-A). */
+#define KO_SCHEME_AOS 0         /* one AOS step of Eq. 4 per level             */
+#define KO_SCHEME_FED 1         /* one FED cycle of explicit steps, Eq. 5      */
+
 /* Hessian normalisation selector, Eq. 8 (see ko_doh). */
 #define KO_DOH_SIGMA4 0         /* s_i^4 * det, s_i = max(1, round(sigma_i)) */
 #define KO_DOH_PAPER_LITERAL 1  /* (sigma_i / 2^o_i)^2 * det                 */
@@ -39,6 +43,8 @@ typedef struct {
     double edge_r;              /* edge ratio r of Eq. 12; <= 0 disables       */
     int doh_norm;               /* KO_DOH_*                                    */
     double k_override;          /* > 0: use this k instead of the histogram    */
+    int scheme;                 /* KO_SCHEME_AOS (default) or KO_SCHEME_FED    */
+    double fed_tau_max;         /* FED stability limit tau_max (0.25)          */
 } ko_options;
 
 typedef struct {
@@ -84,7 +90,27 @@ void ko_thomas(int n, const double* a, const double* b, const double* c,
 void ko_aos_step(const double* Lprev, const double* g, int W, int H,
                  double tau, double* ux, double* uy, double* Lnext);
 
-/* Whole nonlinear scale space (Sec. II-A): presmoothing, k, N-1 AOS steps.
+/* Eq. 5, readings F1-F3: the step sizes of one FED cycle that reaches the
+ * stopping time dt.  n is the smallest cycle length whose stopping time
+ * tau_max (n^2 + n) / 3 reaches dt; tau_j = tau_max / (2 cos^2(pi (2j + 1) /
+ * (4n + 2))) for j = 0..n-1, all scaled by dt / (tau_max (n^2 + n) / 3) so
+ * that they sum to dt.  Writes min(n, cap) sizes and returns n (0 when
+ * dt <= 0). */
+int ko_fed_tau(double dt, double tau_max, double* tau, int cap);
+
+/* One explicit diffusion step with the conductance g held fixed (F4):
+ * out = L + tau * sum over the 4-neighbours q of (g_p + g_q)/2 (L_q - L_p);
+ * a neighbour outside the image contributes nothing (no flux through the
+ * border, the Neumann condition of the AOS step).  out may not alias L. */
+void ko_fed_step(const double* L, const double* g, int W, int H, double tau, double* out);
+
+/* One FED cycle: the steps of ko_fed_tau(dt, tau_max) in order from L.
+ * Returns the number of steps. */
+int ko_fed_evolve(const double* L, const double* g, int W, int H, double dt, double tau_max,
+                  double* out);
+
+/* Whole nonlinear scale space (Sec. II-A): presmoothing, k, N-1 AOS steps
+ * (or FED cycles with opt->scheme == KO_SCHEME_FED).
  * levels holds N*W*H doubles.  Returns 0 on success. */
 int ko_build_scale_space(const double* img, int W, int H, const ko_options* opt,
                          double* levels, double* k_used);
