@@ -168,6 +168,7 @@ KIND_SOURCES = {
     "aos_rows": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
     "aos_cols": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
     "doh": ["k_detector.cu"], "extrema": ["k_detector.cu"], "describe": ["k_describe.cu"],
+    "fed": ["k_fed.cu"],
 }
 
 
@@ -367,6 +368,7 @@ def run_ours(args, rank, world, local_rank):
     traffic = ncu_traffic(dom)
 
     describe = run_describe(args, k, torch, stream, flush, k.detect(x), slowest, barrier)
+    fed = run_fed(args, kaze, torch, img, flush, slowest, barrier, t_dev_ms / args.steps)
     batched = None if args.no_batch else run_batched(args, kaze, synth, torch, stream, world, rank,
                                                         slowest, barrier)
     surrogate = None if args.no_surrogate else run_surrogate(args, kaze, synth, torch, rank)
@@ -405,6 +407,7 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes},
         "kernels": kernels,
         "describe": describe,
+        "fed": fed,
         "batched": batched,
         "surrogate": surrogate,
         "cpu_baseline": cpu,
@@ -414,6 +417,39 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
     k.close()
     return 0
+
+
+def run_fed(args, kaze, torch, img, flush, max_over_ranks, barrier, aos_ms):
+    """The same detection with the FED evolution of Eq. 5 (the paper's own
+    GPU scheme: one cycle of explicit steps per level) instead of AOS,
+    graph-replayed, L2 flushed before every step."""
+    k = kaze.Kaze(W_IMG, H_IMG, octaves=OCTAVES, sublevels=SUBLEVELS, scheme=kaze.SCHEME_FED)
+    x = torch.from_numpy(img).cuda()
+    for _ in range(args.warmup):
+        k.detect(x)
+    n_kp = len(k.detect(x))
+    launches = k.last_launch_count()
+    reps = max(3, min(args.steps, 50))
+    st = k.stream
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    barrier()
+    with torch.cuda.stream(st):
+        for i in range(reps):
+            flush.zero_()
+            starts[i].record(st)
+            k.detect(x)
+            ends[i].record(st)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / reps)
+    prof = k.profile(x)
+    k.close()
+    fed_ms, fed_n = prof.get("fed", (0.0, 0))
+    return {"ms_per_step": ms, "mpix_per_s": W_IMG * H_IMG / (ms * 1e-3) / 1e6, "keypoints": n_kp,
+            "launches_per_step": launches, "explicit_steps": fed_n,
+            "ms_per_explicit_step": fed_ms / fed_n if fed_n else None,
+            "explicit_step_algorithmic_gbs": (12 * W_IMG * H_IMG / (fed_ms / fed_n * 1e-3) / 1e9) if fed_n else None,
+            "aos_ms_per_step": aos_ms, "aos_over_fed_speed": ms / aos_ms}
 
 
 def run_describe(args, k, torch, stream, flush, kp, max_over_ranks, barrier):

@@ -54,6 +54,13 @@ typedef enum {
 #define KAZE_G1 1  /* g1 = exp(-|grad L_sigma|^2 / k^2)         */
 #define KAZE_G2 2  /* g2 = 1 / (1 + |grad L_sigma|^2 / k^2)     */
 
+/* Evolution scheme of each level (Sec. II-A). */
+#define KAZE_SCHEME_AOS 0  /* one AOS step of Eq. 4 per level (default)                    */
+#define KAZE_SCHEME_FED 1  /* one FED cycle of explicit steps per level (Eq. 5): the n with
+                              cycle time fed_tau_max (n^2 + n) / 3 >= t_i - t_{i-1}, steps
+                              tau_j of Eq. 5 scaled to sum to t_i - t_{i-1}, conductance of
+                              the previous level held fixed over the cycle                 */
+
 /* Normalisation of the Hessian determinant, Eq. 8. */
 #define KAZE_DOH_SIGMA4 0         /* s_i^4 det, s_i = max(1, round(sigma_i)) (default) */
 #define KAZE_DOH_PAPER_LITERAL 1  /* (sigma_i / 2^o_i)^2 det, as Eq. 8 is printed      */
@@ -71,6 +78,8 @@ typedef struct kaze_options {
     int doh_norm;         /* KAZE_DOH_*                                           */
     float k_override;     /* > 0: use this contrast factor, skip the histogram    */
     int max_keypoints;    /* capacity of the device keypoint buffer (65536)       */
+    int scheme;           /* KAZE_SCHEME_AOS (default) or KAZE_SCHEME_FED         */
+    float fed_tau_max;    /* FED stability limit, (0, 0.25] (0.25)                */
 } kaze_options;
 
 /* One detected keypoint (Sec. II-B). */
@@ -210,6 +219,15 @@ kaze_status kaze_op_conductance(kaze_handle* h, const float* d_L, float* d_g, in
  * device wait as KAZE_ERR_TIMEOUT). */
 kaze_status kaze_op_aos_step(kaze_handle* h, const float* d_Lprev, const float* d_g,
                              float* d_ux, float* d_Lnext, int pitch, int w, int h_, float tau);
+
+/* One FED cycle (Eq. 5) from d_Lprev to stopping time dt with the
+ * conductance d_g held fixed: n explicit steps of the handle's scheme
+ * (fed_tau_max), alternating between d_scratch and d_Lnext and ending in
+ * d_Lnext.  All buffers share pitch (a multiple of 4) and start on 16-byte
+ * boundaries; outputs must not alias inputs or each other.  *n_steps (may be
+ * NULL) receives n.  Async. */
+kaze_status kaze_op_fed_cycle(kaze_handle* h, const float* d_Lprev, const float* d_g, float* d_scratch,
+                              float* d_Lnext, int pitch, int w, int h_, float dt, int* n_steps);
 
 /* Detector response of Eq. 8 of one level: step s = max(1, round(sigma_i)),
  * normalisation by the handle's doh_norm.  Async. */

@@ -125,6 +125,7 @@ def _load():
         "ko_thomas": (None, [i, dp, dp, dp, dp, dp]),
         "ko_aos_step": (None, [dp, dp, i, i, d, dp, dp, dp]),
         "ko_fed_tau": (i, [d, d, dp, i]),
+        "ko_fed_order": (i, [i, dp, ctypes.POINTER(ctypes.c_int)]),
         "ko_fed_step": (None, [dp, dp, i, i, d, dp]),
         "ko_fed_evolve": (i, [dp, dp, i, i, d, d, dp]),
         "ko_build_scale_space": (i, [dp, i, i, ctypes.POINTER(Options), dp, dp]),
@@ -241,6 +242,16 @@ def fed_tau(dt: float, tau_max: float = 0.25) -> np.ndarray:
     t, tp = _out((max(n, 1),))
     _load().ko_fed_tau(dt, tau_max, tp, n)
     return t[:n]
+
+
+def fed_order(dt: float, tau_max: float = 0.25):
+    """(order, kappa): the step order of the FED cycle reaching dt (reading F5)."""
+    t = fed_tau(dt, tau_max)
+    n = len(t)
+    order = (ctypes.c_int * max(n, 1))()
+    tt, tp = _c(t if n else np.zeros(1))
+    kappa = _load().ko_fed_order(n, tp, order)
+    return np.array(order[:n], dtype=np.int64), int(kappa)
 
 
 def fed_step(L, g, tau: float) -> np.ndarray:

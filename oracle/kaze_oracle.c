@@ -287,6 +287,71 @@ int ko_fed_tau(double dt, double tau_max, double* tau, int cap)
     return n;
 }
 
+static int is_prime(int q)
+{
+    if (q < 2) return 0;
+    for (int d = 2; d * d <= q; ++d)
+        if (q % d == 0) return 0;
+    return 1;
+}
+
+/* The kappa-cycle permutation: position l takes step (kappa (l+1) mod p) - 1. */
+static void kappa_cycle(int n, int kappa, int* order)
+{
+    int p = n + 1;
+    while (!is_prime(p)) ++p;
+    int m = 0;
+    for (int l = 0; m < n; ++l) {
+        int idx = (int)(((long long)(l + 1) * kappa) % p) - 1;
+        if (idx >= 0 && idx < n) order[m++] = idx;
+    }
+}
+
+/* Worst-case rounding amplification of the steps in this order (F5). */
+static double order_amplification(int n, const double* tau, const int* order)
+{
+    const int G = 2000;
+    double* head = (double*)malloc(sizeof(double) * (size_t)n);
+    double* tail = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int j = 0; j < n; ++j) head[j] = tail[j] = 0.0;
+    for (int gi = 0; gi <= G; ++gi) {
+        const double x = 8.0 * gi / G;
+        double pr = 1.0;
+        for (int j = 0; j < n; ++j) {          /* steps 0..j */
+            pr *= fabs(1.0 - tau[order[j]] * x);
+            if (pr > head[j]) head[j] = pr;
+        }
+        pr = 1.0;
+        for (int j = n - 1; j >= 0; --j) {     /* steps j+1..n-1 */
+            if (pr > tail[j]) tail[j] = pr;
+            pr *= fabs(1.0 - tau[order[j]] * x);
+        }
+    }
+    double b = 0.0;
+    for (int j = 0; j < n; ++j) b += head[j] * tail[j];
+    free(head); free(tail);
+    return b;
+}
+
+int ko_fed_order(int n, const double* tau, int* order)
+{
+    if (n <= 0) return 0;
+    int* cand = (int*)malloc(sizeof(int) * (size_t)n);
+    double best = -1.0;
+    int bk = 1;
+    for (int kappa = 1; kappa <= n; ++kappa) {
+        kappa_cycle(n, kappa, cand);
+        const double b = order_amplification(n, tau, cand);
+        if (best < 0.0 || b < best) {
+            best = b;
+            bk = kappa;
+        }
+    }
+    kappa_cycle(n, bk, order);
+    free(cand);
+    return bk;
+}
+
 /* F4: explicit step of div(g grad L) in the flux form of the AOS operator. */
 void ko_fed_step(const double* L, const double* g, int W, int H, double tau, double* out)
 {
@@ -309,17 +374,19 @@ int ko_fed_evolve(const double* L, const double* g, int W, int H, double dt, dou
     int n = ko_fed_tau(dt, tau_max, NULL, 0);
     double* tau = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     ko_fed_tau(dt, tau_max, tau, n);
+    int* order = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    ko_fed_order(n, tau, order);
     double* a = (double*)malloc(sizeof(double) * P);
     double* b = (double*)malloc(sizeof(double) * P);
     memcpy(a, L, sizeof(double) * P);
     for (int j = 0; j < n; ++j) {
-        ko_fed_step(a, g, W, H, tau[j], b);
+        ko_fed_step(a, g, W, H, tau[order[j]], b);
         double* t = a;
         a = b;
         b = t;
     }
     memcpy(out, a, sizeof(double) * P);
-    free(a); free(b); free(tau);
+    free(a); free(b); free(tau); free(order);
     return n;
 }
 

@@ -1,0 +1,232 @@
+// k_fed.cu -- the FED evolution of Sec. II-A (Eq. 5): each level is reached
+// from the previous one by a cycle of n explicit diffusion steps of varying
+// size tau_j, with the conductance g of the previous level held fixed:
+//     L <- L + tau_j * sum over the 4-neighbours q of (g_p + g_q)/2 (L_q - L_p),
+// a neighbour outside the image contributing nothing (no flux through the
+// border, the Neumann condition of the AOS step).
+//
+// The steps of a cycle are taken in a kappa-cycle order (Grewenig, Weickert
+// & Bruhn 2010): the cycle is exact in any order, but in FP32 the natural
+// increasing order lets the last, largest steps amplify early rounding errors
+// by up to ~1e13 for n = 29; the kappa with the smallest worst-case
+// amplification (~1e2 there) is taken.
+//
+// One launch per step.  A warp owns 128 consecutive columns (four per lane,
+// 16-byte loads) and walks FR consecutive rows, keeping the rows above, at
+// and below the current one of L and g in registers (each row is loaded once
+// per walk, FDP rows ahead); horizontal neighbours come from the adjacent
+// lanes by shuffles, the two columns beyond the warp's ends by scalar loads
+// of the end lanes.  Planes need 16-byte aligned rows (pitch % 4 == 0).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "kaze_internal.h"
+
+namespace kz {
+namespace {
+
+constexpr int FR = 16;        // rows per warp
+constexpr int FW = 4;         // warps per CTA, side by side
+constexpr int FDP = 2;        // rows of loads in flight ahead of the arithmetic
+
+struct Row {
+    float4 L, g;
+    float lL, lg, rL, rg;     // the columns left of lane 0 / right of lane 31
+};
+
+__device__ __forceinline__ Row load_row(const float* __restrict__ L, const float* __restrict__ g, int pitch, int w,
+                                        int h, int y, int x0, int lane)
+{
+    Row r;
+    const int yy = min(max(y, 0), h - 1);  // rows outside carry no flux; any valid row will do
+    const size_t o = (size_t)yy * pitch + x0;
+    if (x0 < w) {
+        r.L = __ldg(reinterpret_cast<const float4*>(L + o));
+        r.g = __ldg(reinterpret_cast<const float4*>(g + o));
+    } else {
+        r.L = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.g = r.L;
+    }
+    r.lL = r.lg = r.rL = r.rg = 0.f;
+    if (lane == 0 && x0 > 0 && x0 - 1 < w) {
+        r.lL = __ldg(L + o - 1);
+        r.lg = __ldg(g + o - 1);
+    }
+    if (lane == 31 && x0 + 4 < w) {
+        r.rL = __ldg(L + o + 4);
+        r.rg = __ldg(g + o + 4);
+    }
+    return r;
+}
+
+// flux of one pixel: c = centre, (l, r, u, d) neighbours with their g, masks
+// for the neighbours that exist
+__device__ __forceinline__ float fed_flux(float Lc, float gc, float Ll, float gl, float Lr, float gr, float Lu,
+                                          float gu, float Ld, float gd, bool hl, bool hr, bool hu, bool hd)
+{
+    float f = 0.f;
+    if (hl) f = fmaf(0.5f * (gc + gl), Ll - Lc, f);
+    if (hr) f = fmaf(0.5f * (gc + gr), Lr - Lc, f);
+    if (hu) f = fmaf(0.5f * (gc + gu), Lu - Lc, f);
+    if (hd) f = fmaf(0.5f * (gc + gd), Ld - Lc, f);
+    return f;
+}
+
+__global__ void __launch_bounds__(FW * 32) k_fed_step(const float* __restrict__ Lin, const float* __restrict__ g,
+                                                      float* __restrict__ Lout, int pitch, int w, int h, float tau)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * FW + warp) * 128 + 4 * lane;
+    const int y0 = blockIdx.y * FR;
+    if ((blockIdx.x * FW + warp) * 128 >= w) return;  // whole warp beyond the image
+    // rows y0 - 1 .. y0 + FR: a ring of FDP + 3 rows
+    Row ring[FDP + 3];
+#pragma unroll
+    for (int i = 0; i < FDP + 2; ++i) ring[i] = load_row(Lin, g, pitch, w, h, y0 - 1 + i, x0, lane);
+#pragma unroll
+    for (int k = 0; k < FR; ++k) {
+        if (k + FDP + 2 <= FR + 1) ring[(k + FDP + 2) % (FDP + 3)] = load_row(Lin, g, pitch, w, h, y0 + k + FDP + 1, x0, lane);
+        const int y = y0 + k;
+        if (y >= h) break;
+        const Row& U = ring[k % (FDP + 3)];
+        const Row& C = ring[(k + 1) % (FDP + 3)];
+        const Row& D = ring[(k + 2) % (FDP + 3)];
+        // left neighbour of component x: the previous lane's w (lane 0: the scalar load)
+        float Ll = __shfl_up_sync(0xffffffffu, C.L.w, 1), gl = __shfl_up_sync(0xffffffffu, C.g.w, 1);
+        float Lr = __shfl_down_sync(0xffffffffu, C.L.x, 1), gr = __shfl_down_sync(0xffffffffu, C.g.x, 1);
+        if (lane == 0) {
+            Ll = C.lL;
+            gl = C.lg;
+        }
+        if (lane == 31) {
+            Lr = C.rL;
+            gr = C.rg;
+        }
+        if (x0 >= w) continue;
+        const bool hu = y > 0, hd = y < h - 1;
+        float4 o;
+        o.x = fmaf(tau, fed_flux(C.L.x, C.g.x, Ll, gl, C.L.y, C.g.y, U.L.x, U.g.x, D.L.x, D.g.x, x0 > 0, x0 + 1 < w, hu,
+                                 hd),
+                   C.L.x);
+        o.y = fmaf(tau, fed_flux(C.L.y, C.g.y, C.L.x, C.g.x, C.L.z, C.g.z, U.L.y, U.g.y, D.L.y, D.g.y, true, x0 + 2 < w,
+                                 hu, hd),
+                   C.L.y);
+        o.z = fmaf(tau, fed_flux(C.L.z, C.g.z, C.L.y, C.g.y, C.L.w, C.g.w, U.L.z, U.g.z, D.L.z, D.g.z, true, x0 + 3 < w,
+                                 hu, hd),
+                   C.L.z);
+        o.w = fmaf(tau, fed_flux(C.L.w, C.g.w, C.L.z, C.g.z, Lr, gr, U.L.w, U.g.w, D.L.w, D.g.w, true, x0 + 4 < w, hu,
+                                 hd),
+                   C.L.w);
+        float* out = Lout + (size_t)y * pitch + x0;
+        if (x0 + 4 <= w) {
+            *reinterpret_cast<float4*>(out) = o;
+        } else {
+            out[0] = o.x;
+            if (x0 + 1 < w) out[1] = o.y;
+            if (x0 + 2 < w) out[2] = o.z;
+        }
+    }
+}
+
+}  // namespace
+
+int fed_cycle(double dt, double tau_max, double* tau, int cap)
+{
+    if (!(dt > 0.0) || !(tau_max > 0.0)) return 0;
+    auto T = [&](int n) { return tau_max * ((double)n * n + n) / 3.0; };
+    int n = (int)std::ceil(std::sqrt(3.0 * dt / tau_max + 0.25) - 0.5);
+    if (n < 1) n = 1;
+    while (T(n) < dt) ++n;
+    while (n > 1 && T(n - 1) >= dt) --n;
+    const double sc = dt / T(n);
+    for (int j = 0; j < n && j < cap; ++j) {
+        const double c = std::cos(3.14159265358979323846 * (2.0 * j + 1.0) / (4.0 * n + 2.0));
+        tau[j] = sc * tau_max / (2.0 * c * c);
+    }
+    return n;
+}
+
+namespace {
+
+bool prime(int q)
+{
+    if (q < 2) return false;
+    for (int d = 2; d * d <= q; ++d)
+        if (q % d == 0) return false;
+    return true;
+}
+
+// Position l of the kappa cycle takes step (kappa (l + 1) mod p) - 1 (p the
+// smallest prime above n; indices outside 0..n-1 are skipped).
+std::vector<int> kappa_order(int n, int kappa)
+{
+    int p = n + 1;
+    while (!prime(p)) ++p;
+    std::vector<int> o;
+    o.reserve((size_t)n);
+    for (long long l = 1; (int)o.size() < n; ++l) {
+        const int i = (int)((l * kappa) % p) - 1;
+        if (i >= 0 && i < n) o.push_back(i);
+    }
+    return o;
+}
+
+// sum over positions j of max_x |prod_{k<=j} (1 - tau x)| * max_x |prod_{k>j} (1 - tau x)|,
+// x over 2001 points of [0, 8]: how far later steps can amplify a rounding
+// error made at step j, times the size the iterate can reach there.
+double amplification(const std::vector<double>& tau, const std::vector<int>& o)
+{
+    const int n = (int)o.size();
+    std::vector<double> hm((size_t)n, 0.0), tm((size_t)n, 0.0);
+    for (int gi = 0; gi <= 2000; ++gi) {
+        const double x = 8.0 * gi / 2000;
+        double a = 1.0;
+        for (int j = 0; j < n; ++j) {
+            a *= std::fabs(1.0 - tau[(size_t)o[(size_t)j]] * x);
+            hm[(size_t)j] = std::max(hm[(size_t)j], a);
+        }
+        double b = 1.0;
+        for (int j = n - 1; j >= 0; --j) {
+            tm[(size_t)j] = std::max(tm[(size_t)j], b);
+            b *= std::fabs(1.0 - tau[(size_t)o[(size_t)j]] * x);
+        }
+    }
+    double sum = 0.0;
+    for (int j = 0; j < n; ++j) sum += hm[(size_t)j] * tm[(size_t)j];
+    return sum;
+}
+
+}  // namespace
+
+std::vector<double> fed_ordered_steps(double dt, double tau_max)
+{
+    const int n = fed_cycle(dt, tau_max, nullptr, 0);
+    std::vector<double> tau((size_t)n);
+    fed_cycle(dt, tau_max, tau.data(), n);
+    if (n <= 1) return tau;
+    double best = 0.0;
+    std::vector<int> pick;
+    for (int kappa = 1; kappa <= n; ++kappa) {
+        std::vector<int> o = kappa_order(n, kappa);
+        const double a = amplification(tau, o);
+        if (pick.empty() || a < best) {
+            best = a;
+            pick = o;
+        }
+    }
+    std::vector<double> out((size_t)n);
+    for (int j = 0; j < n; ++j) out[(size_t)j] = tau[(size_t)pick[(size_t)j]];
+    return out;
+}
+
+cudaError_t launch_fed_step(const float* Lin, const float* g, float* Lout, int pitch, int w, int h, float tau,
+                            cudaStream_t st)
+{
+    if ((pitch & 3) || (((uintptr_t)Lin | (uintptr_t)g | (uintptr_t)Lout) & 15)) return cudaErrorInvalidValue;
+    dim3 grid((w + FW * 128 - 1) / (FW * 128), (h + FR - 1) / FR);
+    k_fed_step<<<grid, FW * 32, 0, st>>>(Lin, g, Lout, pitch, w, h, tau);
+    return cudaGetLastError();
+}
+
+}  // namespace kz

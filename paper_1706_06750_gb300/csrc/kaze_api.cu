@@ -25,11 +25,11 @@ namespace {
 // Kernel kinds, in pipeline order, for launch counting and profiling.
 enum KernelKind {
     KK_PRESMOOTH = 0, KK_GRAD_MAX, KK_GRAD_HIST, KK_PERCENTILE, KK_SET_SCALAR,
-    KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_SURROGATE, KK_DESCRIBE, KK_COUNT
+    KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_SURROGATE, KK_DESCRIBE, KK_FED, KK_COUNT
 };
 const char* const kKindNames[KK_COUNT] = {
     "presmooth", "grad_max", "grad_hist", "percentile", "set_scalar",
-    "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate", "describe"};
+    "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate", "describe", "fed"};
 }  // namespace
 
 struct kaze_handle {
@@ -68,6 +68,7 @@ struct kaze_handle {
     // scale table (Eq. 6-7) and filter taps
     double sigma[kz::kMaxLevels];
     double t[kz::kMaxLevels];
+    std::vector<float> fed_tau[kz::kMaxLevels];  // FED step sizes of level i's cycle
     kz::GaussTaps taps0, tapsd;
     kz::LevelTable tab;
 
@@ -239,6 +240,21 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
             S.pitch = P;
             S.opitch = P;
             KZ_LAUNCH(h, KK_SURROGATE, kz::sg::enqueue_pipeline_step(h->surrogate, S, h->d_status, st));
+            continue;
+        }
+        if (h->opt.scheme == KAZE_SCHEME_FED) {
+            // one FED cycle: n explicit steps from L_{i-1}, alternating between
+            // the row-solution scratch plane and L_i so that the last lands in L_i
+            KZ_LAUNCH(h, KK_CONDUCTANCE,
+                      kz::launch_conductance(Lp, h->g, nullptr, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
+            const std::vector<float>& tj = h->fed_tau[i];
+            const int n = (int)tj.size();
+            const float* src = Lp;
+            for (int j = 0; j < n; ++j) {
+                float* dst = ((n - 1 - j) % 2 == 0) ? Li : h->ux;
+                KZ_LAUNCH(h, KK_FED, kz::launch_fed_step(src, h->g, dst, P, w, hh, tj[j], st));
+                src = dst;
+            }
             continue;
         }
         // conductance also zeroes L_i; the row and column halves of the AOS
@@ -415,6 +431,8 @@ KAZE_API void kaze_default_options(kaze_options* o)
     o->doh_norm = KAZE_DOH_SIGMA4;
     o->k_override = 0.0f;
     o->max_keypoints = 65536;
+    o->scheme = KAZE_SCHEME_AOS;
+    o->fed_tau_max = 0.25f;
 }
 
 KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, void* cuda_stream,
@@ -435,6 +453,10 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     if (o.doh_norm != KAZE_DOH_SIGMA4 && o.doh_norm != KAZE_DOH_PAPER_LITERAL)
         return create_fail(KAZE_ERR_INVALID_ARG, "unknown doh_norm");
     if (o.max_keypoints < 1) return create_fail(KAZE_ERR_INVALID_ARG, "max_keypoints must be >= 1");
+    if (o.scheme != KAZE_SCHEME_AOS && o.scheme != KAZE_SCHEME_FED)
+        return create_fail(KAZE_ERR_INVALID_ARG, "unknown evolution scheme");
+    if (!(o.fed_tau_max > 0.f && o.fed_tau_max <= 0.25f))
+        return create_fail(KAZE_ERR_INVALID_ARG, "fed_tau_max must lie in (0, 0.25]");
     if (max_w < 3 || max_h < 3 || max_w > 16384 || max_h > 16384)
         return create_fail(KAZE_ERR_INVALID_ARG, "max_w and max_h must be in 3..16384");
     if (kz::aos_rows_smem_bytes(max_w) == 0 || kz::aos_cols_smem_bytes(max_h) == 0)
@@ -470,6 +492,10 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
             }
         }
 
+    for (int i = 1; i < N; ++i) {
+        const std::vector<double> tj = kz::fed_ordered_steps(h->t[i] - h->t[i - 1], (double)o.fed_tau_max);
+        h->fed_tau[i].assign(tj.begin(), tj.end());
+    }
     {
         cudaError_t ce = kz::configure_filter_kernels();
         const char* what = "configure_filter_kernels";
@@ -633,6 +659,34 @@ KAZE_API kaze_status kaze_detect_host(kaze_handle* h, const float* h_img, int w,
                                 sizeof(float) * w, hh, cudaMemcpyHostToDevice, h->stream));
     KZ_CHECK(run_detect_graph(h, h->staging, w, hh, sp));
     return collect_keypoints(h, h_out, capacity, count);
+}
+
+KAZE_API kaze_status kaze_op_fed_cycle(kaze_handle* h, const float* d_Lprev, const float* d_g, float* d_scratch,
+                                       float* d_Lnext, int pitch, int w, int hh, float dt, int* n_steps)
+{
+    if (!h || !d_Lprev || !d_g || !d_scratch || !d_Lnext) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch < w || pitch % 4) return fail(h, KAZE_ERR_INVALID_ARG, "pitch must be >= w and a multiple of 4");
+    const uintptr_t al = (uintptr_t)d_Lprev | (uintptr_t)d_g | (uintptr_t)d_scratch | (uintptr_t)d_Lnext;
+    if (al & 15) return fail(h, KAZE_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    if (d_Lnext == d_Lprev || d_Lnext == d_g || d_scratch == d_Lprev || d_scratch == d_g || d_scratch == d_Lnext)
+        return fail(h, KAZE_ERR_INVALID_ARG, "outputs alias inputs");
+    if (!(dt >= 0.f) || !std::isfinite(dt)) return fail(h, KAZE_ERR_INVALID_ARG, "bad stopping time");
+    const std::vector<double> tj = kz::fed_ordered_steps((double)dt, (double)h->opt.fed_tau_max);
+    const int n = (int)tj.size();
+    h->launches = 0;
+    if (n == 0) {
+        KZ_TRY(h, cudaMemcpy2DAsync(d_Lnext, sizeof(float) * pitch, d_Lprev, sizeof(float) * pitch, sizeof(float) * w,
+                                    hh, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    const float* src = d_Lprev;
+    for (int j = 0; j < n; ++j) {
+        float* dst = ((n - 1 - j) % 2 == 0) ? d_Lnext : d_scratch;
+        KZ_LAUNCH(h, KK_FED, kz::launch_fed_step(src, d_g, dst, pitch, w, hh, (float)tj[j], h->stream));
+        src = dst;
+    }
+    if (n_steps) *n_steps = n;
+    return KAZE_OK;
 }
 
 // ---- description (Sec. II-C) -------------------------------------------------

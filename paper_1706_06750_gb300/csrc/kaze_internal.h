@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "kaze.h"
 
 namespace kz {
@@ -142,6 +144,18 @@ cudaError_t launch_extrema(const float* D, int pitch, long long plane_stride, in
                            int n, const LevelTable& tab, float dthreshold, float edge_r,
                            kaze_keypoint* d_kp, int cap, unsigned int* d_count,
                            cudaStream_t st);
+
+// FED (Eq. 5): the step sizes of one cycle reaching stopping time dt with
+// stability limit tau_max (the smallest n whose cycle time tau_max (n^2+n)/3
+// reaches dt, sizes scaled to sum to dt); writes min(n, cap), returns n.
+int fed_cycle(double dt, double tau_max, double* tau, int cap);
+// The same sizes in the step order the library takes them (kappa cycle of
+// the smallest worst-case rounding amplification).
+std::vector<double> fed_ordered_steps(double dt, double tau_max);
+// One explicit step L_out = L_in + tau div(g grad L_in) (flux form, no flux
+// through the border); rows 16-byte aligned, pitch % 4 == 0.
+cudaError_t launch_fed_step(const float* Lin, const float* g, float* Lout, int pitch, int w, int h, float tau,
+                            cudaStream_t st);
 
 // Orientation and 64-D M-SURF descriptor of n device keypoints (angle
 // written back into d_kps, descriptors to d_desc, n x 64); keypoint k lies on

@@ -26,6 +26,8 @@ G1 = 1
 G2 = 2
 DOH_SIGMA4 = 0
 DOH_PAPER_LITERAL = 1
+SCHEME_AOS = 0
+SCHEME_FED = 1
 
 
 class KazeError(RuntimeError):
@@ -48,6 +50,8 @@ class Options(ctypes.Structure):
         ("doh_norm", ctypes.c_int),
         ("k_override", ctypes.c_float),
         ("max_keypoints", ctypes.c_int),
+        ("scheme", ctypes.c_int),
+        ("fed_tau_max", ctypes.c_float),
     ]
 
 
@@ -138,6 +142,7 @@ _SIGNATURES = {
     "kaze_kernel_name": (ctypes.c_char_p, [_i]),
     "kaze_last_launch_count": (_i, [_vp]),
     "kaze_profile": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)]),
+    "kaze_op_fed_cycle": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _f, ctypes.POINTER(_i)]),
     "kaze_describe": (_i, [_vp, _vp, _i, _vp, _i]),
     "kaze_describe_device": (_i, [_vp, _vp, _i, _vp, _i]),
     "kaze_op_describe": (_i, [_vp, _vp, _i, _i, _i, _f, _vp, _i, _vp, _i]),
@@ -519,6 +524,18 @@ class Kaze:
                                           _vp(ux.data_ptr()), _vp(Lnext.data_ptr()), pitch, w, h,
                                           float(tau)), "kaze_op_aos_step")
         self._end()
+
+    def op_fed_cycle(self, Lprev, g, scratch, Lnext, dt):
+        """One FED cycle (Eq. 5) from Lprev to stopping time dt with g fixed;
+        returns the number of explicit steps."""
+        w, h, pitch = _check_image(Lprev)
+        n = _i()
+        self._begin()
+        self._ck(self._L.kaze_op_fed_cycle(self._h, _vp(Lprev.data_ptr()), _vp(g.data_ptr()),
+                                           _vp(scratch.data_ptr()), _vp(Lnext.data_ptr()), pitch, w, h,
+                                           float(dt), ctypes.byref(n)), "kaze_op_fed_cycle")
+        self._end()
+        return int(n.value)
 
     def op_doh(self, L, D, sigma_i, octave):
         w, h, pitch = _check_image(L)

@@ -133,3 +133,32 @@ def test_scale_space_with_fed():
     # AOS and FED levels are close (same diffusion, different discretisation)
     lv_a, _ = oracle.build_scale_space(img, oracle.Options.make(octaves=2, sublevels=3))
     assert np.max(np.abs(lv - lv_a)) < 0.05
+
+
+def _amplification(t, lam=np.linspace(0.0, 8.0, 4001)):
+    f = [np.abs(1.0 - tk * lam) for tk in t]
+    b = 0.0
+    for j in range(len(t)):
+        head = np.prod(f[: j + 1], axis=0).max()
+        tail = np.prod(f[j + 1:], axis=0).max() if j + 1 < len(t) else 1.0
+        b += head * tail
+    return b
+
+
+def test_kappa_cycle_order():
+    # hand-worked kappa cycle: n = 4, p = 5, kappa = 2 gives 1, 3, 0, 2
+    t = oracle.fed_tau(cycle_time(4))
+    order, kappa = oracle.fed_order(cycle_time(4))
+    assert sorted(order) == [0, 1, 2, 3]
+    p = 5
+    seq = [((l + 1) * kappa) % p - 1 for l in range(p - 1)]
+    assert list(order) == [i for i in seq if 0 <= i < 4]
+    # long cycles: the chosen order keeps FP32 rounding bounded where the
+    # natural (increasing) order would amplify it beyond any use
+    for dt in (5.0, 20.0, 67.9):
+        t = oracle.fed_tau(dt)
+        order, _ = oracle.fed_order(dt)
+        assert sorted(order) == list(range(len(t)))
+        b_nat, b_ord = _amplification(t), _amplification(t[order])
+        assert b_ord < 1e3 and b_ord < b_nat, (dt, b_nat, b_ord)
+        assert len(t) < 15 or b_ord < b_nat / 1e4, (dt, b_nat, b_ord)
