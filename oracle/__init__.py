@@ -36,6 +36,8 @@ DOH_SIGMA4 = 0
 DOH_PAPER_LITERAL = 1
 SCHEME_AOS = 0
 SCHEME_FED = 1
+EXTREMA_3X3 = 0
+EXTREMA_SIGMA_WINDOW = 1
 
 
 class Options(ctypes.Structure):
@@ -55,14 +57,16 @@ class Options(ctypes.Structure):
         ("k_override", ctypes.c_double),
         ("scheme", ctypes.c_int),
         ("fed_tau_max", ctypes.c_double),
+        ("extrema_window", ctypes.c_int),
     ]
 
     @classmethod
     def make(cls, octaves=4, sublevels=4, sigma0=1.6, sigma_d=1.0,
              k_percentile=0.7, nbins=300, diffusivity=G2, dthreshold=0.001,
-             edge_r=10.0, doh_norm=DOH_SIGMA4, k_override=0.0, scheme=0, fed_tau_max=0.25):
+             edge_r=10.0, doh_norm=DOH_SIGMA4, k_override=0.0, scheme=0, fed_tau_max=0.25, extrema_window=0):
         return cls(octaves, sublevels, sigma0, sigma_d, k_percentile, nbins,
-                   diffusivity, dthreshold, edge_r, doh_norm, k_override, scheme, fed_tau_max)
+                   diffusivity, dthreshold, edge_r, doh_norm, k_override, scheme, fed_tau_max,
+                   extrema_window)
 
 
 class Keypoint(ctypes.Structure):
@@ -132,7 +136,7 @@ def _load():
         "ko_step_size": (i, [d]),
         "ko_hessian": (None, [dp, i, i, i, dp, dp, dp]),
         "ko_doh": (None, [dp, i, i, d, i, i, dp]),
-        "ko_find_extrema": (i, [dp, i, i, i, i, dp, d, d,
+        "ko_find_extrema": (i, [dp, i, i, i, i, dp, d, d, i,
                                 ctypes.POINTER(Keypoint), i]),
     }
     for name, (res, args) in sig.items():
@@ -327,7 +331,7 @@ def find_extrema(D, opt: Options | None = None, cap: int = 1 << 20) -> np.ndarra
     sig, sp = _c(sig[:n])
     out = (Keypoint * max(cap, 1))()
     cnt = _load().ko_find_extrema(dp, w, h, n, opt.sublevels, sp, opt.dthreshold,
-                                  opt.edge_r, out, cap)
+                                  opt.edge_r, opt.extrema_window, out, cap)
     if cnt > cap:
         raise ValueError(f"{cnt} keypoints exceed cap {cap}")
     arr = np.frombuffer(out, dtype=KEYPOINT_DTYPE, count=cnt).copy()

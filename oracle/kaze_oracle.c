@@ -489,25 +489,41 @@ void ko_doh(const double* L, int W, int H, double sigma_i, int octave,
     free(xx); free(yy); free(xy);
 }
 
-/* Sec. II-B and Sec. III-2 (readings R7, R8, R9). */
+/* Sec. II-B and Sec. III-2 (readings R7, R8, R9, W1). */
 int ko_find_extrema(const double* D, int W, int H, int N, int S,
                     const double* sigma, double dthreshold, double edge_r,
-                    ko_keypoint* out, int cap)
+                    int window, ko_keypoint* out, int cap)
 {
     size_t P = (size_t)W * H;
     int count = 0;
     for (int i = 1; i <= N - 2; ++i) {
         const double* Dc = D + (size_t)i * P;
+        int r = 1;
+        if (window == KO_EXTREMA_SIGMA_WINDOW) {
+            r = ko_step_size(sigma[i]) / 2;
+            if (r < 1) r = 1;
+        }
         for (int y = 1; y <= H - 2; ++y)
             for (int x = 1; x <= W - 2; ++x) {
                 double v = Dc[(size_t)y * W + x];
                 if (!(v > dthreshold)) continue;
                 int is_max = 1;
-                for (int l = i - 1; l <= i + 1 && is_max; ++l)
-                    for (int dy = -1; dy <= 1 && is_max; ++dy)
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            if (l == i && dx == 0 && dy == 0) continue;
-                            if (!(v > D[(size_t)l * P + (size_t)(y + dy) * W + (x + dx)])) {
+                /* the 8 neighbours on the level itself */
+                for (int dy = -1; dy <= 1 && is_max; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (dx == 0 && dy == 0) continue;
+                        if (!(v > Dc[(size_t)(y + dy) * W + (x + dx)])) {
+                            is_max = 0;
+                            break;
+                        }
+                    }
+                /* the window directly below and above */
+                for (int l = i - 1; l <= i + 1 && is_max; l += 2)
+                    for (int dy = -r; dy <= r && is_max; ++dy)
+                        for (int dx = -r; dx <= r; ++dx) {
+                            int xx = x + dx, yy = y + dy;
+                            if (xx < 0 || xx >= W || yy < 0 || yy >= H) continue;
+                            if (!(v > D[(size_t)l * P + (size_t)yy * W + xx])) {
                                 is_max = 0;
                                 break;
                             }

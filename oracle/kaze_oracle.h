@@ -28,6 +28,10 @@ extern "C" {
 #define KO_SCHEME_AOS 0         /* one AOS step of Eq. 4 per level             */
 #define KO_SCHEME_FED 1         /* one FED cycle of explicit steps, Eq. 5      */
 
+/* Cross-level neighbourhood of the maximum test (Sec. II-B, Sec. IV). */
+#define KO_EXTREMA_3X3 0           /* 3x3 at levels i-1 and i+1 (26 neighbours)  */
+#define KO_EXTREMA_SIGMA_WINDOW 1  /* the sigma x sigma window at levels i +- 1  */
+
 /* Hessian normalisation selector, Eq. 8 (see ko_doh). */
 #define KO_DOH_SIGMA4 0         /* s_i^4 * det, s_i = max(1, round(sigma_i)) */
 #define KO_DOH_PAPER_LITERAL 1  /* (sigma_i / 2^o_i)^2 * det                 */
@@ -45,6 +49,7 @@ typedef struct {
     double k_override;          /* > 0: use this k instead of the histogram    */
     int scheme;                 /* KO_SCHEME_AOS (default) or KO_SCHEME_FED    */
     double fed_tau_max;         /* FED stability limit tau_max (0.25)          */
+    int extrema_window;         /* KO_EXTREMA_3X3 (default) or _SIGMA_WINDOW  */
 } ko_options;
 
 typedef struct {
@@ -139,12 +144,16 @@ void ko_hessian(const double* L, int W, int H, int s,
 void ko_doh(const double* L, int W, int H, double sigma_i, int octave,
             int doh_norm, double* D);
 
-/* 3x3x3 maxima with sub-pixel fit and edge test (Sec. II-B, Eq. 9-12).
- * D holds N*W*H responses.  Writes at most cap keypoints, returns the total
- * number found (which may exceed cap). */
+/* Maxima with sub-pixel fit and edge test (Sec. II-B, Eq. 9-12): above the
+ * threshold, strictly above the 8 neighbours at level i and above every
+ * response of levels i-1 and i+1 within |dx|, |dy| <= r_i: r_i = 1 (the 3x3x3
+ * test), or with window = KO_EXTREMA_SIGMA_WINDOW (reading W1) the sigma_i x
+ * sigma_i window r_i = max(1, floor(s_i / 2)), s_i = max(1, round(sigma_i)),
+ * pixels outside the image skipped.  D holds N*W*H responses.  Writes at most
+ * cap keypoints, returns the total number found (which may exceed cap). */
 int ko_find_extrema(const double* D, int W, int H, int N, int S,
                     const double* sigma, double dthreshold, double edge_r,
-                    ko_keypoint* out, int cap);
+                    int window, ko_keypoint* out, int cap);
 
 #ifdef __cplusplus
 }

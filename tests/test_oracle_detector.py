@@ -175,3 +175,52 @@ def test_edge_test_threshold_uses_trace_of_both_curvatures(oracle_mod, ratio, ke
     D = np.stack([0.5 * peak, peak, 0.5 * peak])
     opt = oracle_mod.Options.make(octaves=1, sublevels=3, edge_r=10.0)
     assert (len(oracle_mod.find_extrema(D, opt)) == 1) == kept
+
+
+# --- the sigma x sigma cross-level window (reading W1) ----------------------
+
+def _stack(seed, n=8, h=40, w=44):
+    from scipy import ndimage
+    rng = np.random.default_rng(seed)
+    return np.stack([ndimage.gaussian_filter(rng.random((h, w)), 1.2) * 0.01 for _ in range(n)])
+
+
+def test_sigma_window_is_the_3x3_test_when_windows_are_3x3(oracle_mod):
+    oracle = oracle_mod
+    # s_i <= 3 on every level (sigma0 = 0.5): r_i = 1, the two tests coincide
+    D = _stack(41)
+    o3 = oracle.Options.make(octaves=2, sublevels=4, sigma0=0.5, dthreshold=0.0, edge_r=0.0)
+    ow = oracle.Options.make(octaves=2, sublevels=4, sigma0=0.5, dthreshold=0.0, edge_r=0.0,
+                             extrema_window=oracle.EXTREMA_SIGMA_WINDOW)
+    a, b = oracle.find_extrema(D, o3), oracle.find_extrema(D, ow)
+    assert len(a) > 10 and np.array_equal(a, b)
+
+
+def test_sigma_window_keeps_a_subset(oracle_mod):
+    oracle = oracle_mod
+    D = _stack(42)
+    o3 = oracle.Options.make(octaves=2, sublevels=4, dthreshold=0.0, edge_r=0.0)
+    ow = oracle.Options.make(octaves=2, sublevels=4, dthreshold=0.0, edge_r=0.0,
+                             extrema_window=oracle.EXTREMA_SIGMA_WINDOW)
+    a, b = oracle.find_extrema(D, o3), oracle.find_extrema(D, ow)
+    ka = {(int(k["level"]), int(k["ix"]), int(k["iy"])) for k in a}
+    kb = {(int(k["level"]), int(k["ix"]), int(k["iy"])) for k in b}
+    assert kb <= ka and len(kb) < len(ka)
+
+
+def test_sigma_window_planted(oracle_mod):
+    oracle = oracle_mod
+    # level 6 of 4 x 4 levels: sigma = 1.6 * 2^1.5 = 4.53, s = 5, r = 2.  A
+    # peak at (20, 20) with a larger value two pixels away one level up is
+    # a 3x3x3 maximum but not a sigma-window maximum; three pixels away it
+    # is outside the window and the peak survives both tests
+    N, h, w = 16, 41, 41
+    for off, keep in ((2, False), (3, True)):
+        D = np.zeros((N, h, w))
+        D[6, 20, 20] = 1.0
+        D[7, 20, 20 + off] = 2.0
+        o3 = oracle.Options.make(dthreshold=0.5, edge_r=0.0)
+        ow = oracle.Options.make(dthreshold=0.5, edge_r=0.0, extrema_window=oracle.EXTREMA_SIGMA_WINDOW)
+        at = lambda kp: any(int(k["level"]) == 6 and int(k["ix"]) == 20 and int(k["iy"]) == 20 for k in kp)
+        assert at(oracle.find_extrema(D, o3))
+        assert at(oracle.find_extrema(D, ow)) == keep
