@@ -61,6 +61,16 @@ typedef enum {
                               tau_j of Eq. 5 scaled to sum to t_i - t_{i-1}, conductance of
                               the previous level held fixed over the cycle                 */
 
+/* Cross-level neighbourhood of the maximum test (Sec. II-B, Sec. IV).  A
+ * candidate is above the threshold and above its 8 neighbours on its level;
+ * it must also lie above every response of levels i-1 and i+1 within |dx|,
+ * |dy| <= r_i (pixels outside the image skipped):                         */
+#define KAZE_EXTREMA_3X3 0           /* r_i = 1, the 3x3x3 test (default)    */
+#define KAZE_EXTREMA_SIGMA_WINDOW 1  /* the sigma_i x sigma_i window:
+                                        r_i = max(1, floor(s_i / 2)),
+                                        s_i = max(1, round(sigma_i)); single-
+                                        image handles only                  */
+
 /* Normalisation of the Hessian determinant, Eq. 8. */
 #define KAZE_DOH_SIGMA4 0         /* s_i^4 det, s_i = max(1, round(sigma_i)) (default) */
 #define KAZE_DOH_PAPER_LITERAL 1  /* (sigma_i / 2^o_i)^2 det, as Eq. 8 is printed      */
@@ -80,6 +90,7 @@ typedef struct kaze_options {
     int max_keypoints;    /* capacity of the device keypoint buffer (65536)       */
     int scheme;           /* KAZE_SCHEME_AOS (default) or KAZE_SCHEME_FED         */
     float fed_tau_max;    /* FED stability limit, (0, 0.25] (0.25)                */
+    int extrema_window;   /* KAZE_EXTREMA_3X3 (default) or _SIGMA_WINDOW          */
 } kaze_options;
 
 /* One detected keypoint (Sec. II-B). */
@@ -253,7 +264,9 @@ kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch, long lo
  * bounded spin, until the stages it reads are complete for its image.  The
  * launch and its set-up are recorded once as a CUDA graph and replayed
  * (except on the legacy or per-thread default stream).  Results match the
- * single-image path. */
+ * single-image path.  Batches evolve by AOS and test 3x3x3 maxima: options
+ * with scheme KAZE_SCHEME_FED or extrema_window KAZE_EXTREMA_SIGMA_WINDOW are
+ * refused (INVALID_ARG). */
 typedef struct kaze_batch kaze_batch;
 
 /* Execution of a batch.

@@ -84,8 +84,9 @@ k_doh(const float* __restrict__ L, float* __restrict__ D, int pitch, long long p
 }
 
 // Each thread tests 4 adjacent pixels (one 16-byte load) of one row of
-// level 1 + blockIdx.z.  Most fail the threshold; survivors read their 26
-// neighbours, fit the quadratic and apply the edge test.
+// level 1 + blockIdx.z.  Most fail the threshold; survivors read their 8
+// neighbours and the (2r+1)^2 responses below and above (r = 1: the 26
+// neighbours of the 3x3x3 test), fit the quadratic and apply the edge test.
 __global__ void __launch_bounds__(256)
 k_extrema(const float* __restrict__ D, int pitch, long long plane_stride, int w, int h,
           const __grid_constant__ LevelTable tab, float thr, float edge_r,
@@ -105,16 +106,31 @@ k_extrema(const float* __restrict__ D, int pitch, long long plane_stride, int w,
         if (!(v > thr) || x < 1 || x > w - 2) continue;
         const size_t p = (size_t)y * pitch + x;
         bool is_max = true;
-        for (int l = -1; l <= 1 && is_max; ++l) {
+        for (int dy = -1; dy <= 1 && is_max; ++dy)  // the 8 neighbours on the level
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                if (!(v > Dc[(long long)p + (long long)dy * pitch + dx])) {
+                    is_max = false;
+                    break;
+                }
+            }
+        // levels i - 1 and i + 1 within |dx|, |dy| <= r (r = 1: the 3x3x3
+        // test; wider for the sigma x sigma window), pixels outside skipped
+        const int r = tab.xr[level];
+        for (int l = -1; l <= 1 && is_max; l += 2) {
             const float* Dl = Dc + (long long)l * plane_stride;
-            for (int dy = -1; dy <= 1 && is_max; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if (l == 0 && dx == 0 && dy == 0) continue;
-                    if (!(v > Dl[(long long)p + (long long)dy * pitch + dx])) {
+            for (int dy = -r; dy <= r && is_max; ++dy) {
+                const int yy = y + dy;
+                if (yy < 0 || yy >= h) continue;
+                for (int dx = -r; dx <= r; ++dx) {
+                    const int xx = x + dx;
+                    if (xx < 0 || xx >= w) continue;
+                    if (!(v > Dl[(long long)yy * pitch + xx])) {
                         is_max = false;
                         break;
                     }
                 }
+            }
         }
         if (!is_max) continue;
         // 3x3 quadratic model of the response around the maximum

@@ -172,6 +172,14 @@ bool make_taps(double sigma, int rmax, kz::GaussTaps* t)
     return true;
 }
 
+// Cross-level radius of the maximum test: 1 (3x3x3), or the sigma x sigma
+// window max(1, floor(s / 2)) for the step s of the level.
+int cross_radius(const kaze_options& o, int step)
+{
+    if (o.extrema_window != KAZE_EXTREMA_SIGMA_WINDOW) return 1;
+    return step / 2 > 1 ? step / 2 : 1;
+}
+
 int step_of(double sigma)
 {
     int s = (int)std::floor(sigma + 0.5);
@@ -433,6 +441,7 @@ KAZE_API void kaze_default_options(kaze_options* o)
     o->max_keypoints = 65536;
     o->scheme = KAZE_SCHEME_AOS;
     o->fed_tau_max = 0.25f;
+    o->extrema_window = KAZE_EXTREMA_3X3;
 }
 
 KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, void* cuda_stream,
@@ -457,6 +466,8 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
         return create_fail(KAZE_ERR_INVALID_ARG, "unknown evolution scheme");
     if (!(o.fed_tau_max > 0.f && o.fed_tau_max <= 0.25f))
         return create_fail(KAZE_ERR_INVALID_ARG, "fed_tau_max must lie in (0, 0.25]");
+    if (o.extrema_window != KAZE_EXTREMA_3X3 && o.extrema_window != KAZE_EXTREMA_SIGMA_WINDOW)
+        return create_fail(KAZE_ERR_INVALID_ARG, "unknown extrema window");
     if (max_w < 3 || max_h < 3 || max_w > 16384 || max_h > 16384)
         return create_fail(KAZE_ERR_INVALID_ARG, "max_w and max_h must be in 3..16384");
     if (kz::aos_rows_smem_bytes(max_w) == 0 || kz::aos_cols_smem_bytes(max_h) == 0)
@@ -484,6 +495,7 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
             const int st = step_of(h->sigma[i]);
             h->tab.step[i] = st;
             h->tab.sigma[i] = (float)h->sigma[i];
+            h->tab.xr[i] = cross_radius(o, st);
             if (o.doh_norm == KAZE_DOH_PAPER_LITERAL) {
                 const double kn = h->sigma[i] / std::pow(2.0, (double)oc);
                 h->tab.norm[i] = (float)(kn * kn);
@@ -880,7 +892,10 @@ KAZE_API kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch
         return fail(h, KAZE_ERR_INVALID_ARG, "responses must be 16-byte aligned with pitch and plane stride % 4 == 0");
     kz::LevelTable t = h->tab;
     t.n = n;
-    for (int i = 0; i < n; ++i) t.sigma[i] = h_sigma[i];
+    for (int i = 0; i < n; ++i) {
+        t.sigma[i] = h_sigma[i];
+        t.xr[i] = cross_radius(h->opt, step_of(h_sigma[i]));
+    }
     KZ_CHECK(enqueue_extrema(h, d_D, pitch, plane_stride, w, hh, n, t));
     return collect_keypoints(h, h_out, capacity, count);
 }

@@ -338,6 +338,8 @@ KAZE_API kaze_status kaze_batch_create(const kaze_options* opt, int n, const int
     if (o.nbins < 1 || o.nbins > kz::kMaxBins || o.max_keypoints < 1) return KAZE_ERR_INVALID_ARG;
     if (o.diffusivity != KAZE_G1 && o.diffusivity != KAZE_G2) return KAZE_ERR_INVALID_ARG;
     if (o.doh_norm != KAZE_DOH_SIGMA4 && o.doh_norm != KAZE_DOH_PAPER_LITERAL) return KAZE_ERR_INVALID_ARG;
+    // the persistent batch kernel evolves by AOS and tests 3x3x3 maxima
+    if (o.scheme != KAZE_SCHEME_AOS || o.extrema_window != KAZE_EXTREMA_3X3) return KAZE_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i)
         if (w[i] < 3 || h[i] < 3 || w[i] > 4096 || h[i] > 4096) return KAZE_ERR_INVALID_ARG;
 

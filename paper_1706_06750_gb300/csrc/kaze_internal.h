@@ -30,6 +30,7 @@ struct LevelTable {
     float norm[kMaxLevels];      // DoH normalisation factor
     float sigma[kMaxLevels];     // sigma_i
     int sublevels;               // S (octave = i / S, sublevel = i % S)
+    int xr[kMaxLevels];          // cross-level radius of the maximum test (1: 3x3x3)
 };
 
 // Per-level constants of keypoint description (Sec. II-C), passed by value.

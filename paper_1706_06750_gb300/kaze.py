@@ -28,6 +28,8 @@ DOH_SIGMA4 = 0
 DOH_PAPER_LITERAL = 1
 SCHEME_AOS = 0
 SCHEME_FED = 1
+EXTREMA_3X3 = 0
+EXTREMA_SIGMA_WINDOW = 1
 
 
 class KazeError(RuntimeError):
@@ -52,6 +54,7 @@ class Options(ctypes.Structure):
         ("max_keypoints", ctypes.c_int),
         ("scheme", ctypes.c_int),
         ("fed_tau_max", ctypes.c_float),
+        ("extrema_window", ctypes.c_int),
     ]
 
 

@@ -351,3 +351,54 @@ def test_full_size_4096x3072_sampled_steps(kz):
         assert np.max(np.abs(host(D) - ref)) <= DOH_REL_TOL * np.max(np.abs(ref))
     assert max(abs(m - means[0]) for m in means) < 1e-5
     assert len(kp) >= 100
+
+
+# ------------------------------------------------- sigma x sigma window --
+
+def test_sigma_window_extrema_on_identical_responses(kz):
+    """The exact cross-level window (reading W1) on the oracle's own FP32
+    responses: comparisons are exact, so the keypoint sets agree up to
+    decisions on a sub-pixel / edge boundary; the window keeps a subset of
+    the 3x3x3 keypoints."""
+    img = synth.workload_image("256x256")
+    opt = oracle.Options.make(octaves=4, sublevels=4)
+    lv, _ = oracle.build_scale_space(img, opt)
+    D = oracle.detector_response(lv, opt).astype(np.float32)
+    sig, _ = oracle.scale_table(4, 4, 1.6)
+    with kz.Kaze(256, 256, octaves=4, sublevels=4, extrema_window=kz.EXTREMA_SIGMA_WINDOW) as k:
+        kp_g = k.op_extrema(dev(D.reshape(-1, 256)).reshape(16, 256, 256), sig)
+    with kz.Kaze(256, 256, octaves=4, sublevels=4) as k:
+        kp_3 = k.op_extrema(dev(D.reshape(-1, 256)).reshape(16, 256, 256), sig)
+    kp_r = oracle.find_extrema(D.astype(np.float64), oracle.Options.make(
+        octaves=4, sublevels=4, dthreshold=float(np.float32(0.001)),
+        extrema_window=oracle.EXTREMA_SIGMA_WINDOW))
+    ov, m, ur, ug, md = compare(kp_r, kp_g, D.astype(np.float64))
+    assert not ur and not ug
+    assert len(kp_r) > 10 and ov == 1.0 and md < 1e-4
+    key = lambda kp: {(int(p["level"]), int(p["ix"]), int(p["iy"])) for p in kp}
+    assert key(kp_g) <= key(kp_3) and len(kp_g) < len(kp_3)
+
+
+def test_sigma_window_pipeline_1920x1200(kz):
+    img = synth.workload_image("1920x1200")
+    with kz.Kaze(1920, 1200, extrema_window=kz.EXTREMA_SIGMA_WINDOW) as k:
+        kp_w = k.detect(dev(img))
+        D = host(k.responses())
+    with kz.Kaze(1920, 1200) as k:
+        kp_3 = k.detect(dev(img))
+    key = lambda kp: {(int(p["level"]), int(p["ix"]), int(p["iy"])) for p in kp}
+    assert key(kp_w) <= key(kp_3) and 0 < len(kp_w) < len(kp_3)
+    # every kept keypoint is above its window one level below and above
+    sig, _ = oracle.scale_table(4, 4, 1.6)
+    for p in kp_w[:200]:
+        i, x, y = int(p["level"]), int(p["ix"]), int(p["iy"])
+        r = max(1, oracle.step_size(sig[i]) // 2)
+        for l in (i - 1, i + 1):
+            win = D[l, max(0, y - r):y + r + 1, max(0, x - r):x + r + 1]
+            assert D[i, y, x] > win.max()
+
+
+def test_batch_refuses_fed_and_window(kz):
+    for bad in (dict(scheme=kz.SCHEME_FED), dict(extrema_window=kz.EXTREMA_SIGMA_WINDOW)):
+        with pytest.raises(kz.KazeError):
+            kz.Batch([(64, 64), (80, 48)], **bad)
