@@ -452,6 +452,43 @@ def run_fed(args, kaze, torch, img, flush, max_over_ranks, barrier, aos_ms):
             "aos_ms_per_step": aos_ms, "aos_over_fed_speed": ms / aos_ms}
 
 
+def run_only(args, local_rank):
+    """One side section (description or FED detection) on the workload
+    image, printed as a JSON line of its own."""
+    import torch
+
+    from paper_1706_06750_gb300 import build, kaze, synth
+    build.build()
+    torch.cuda.set_device(local_rank)
+    img = synth.image(W_IMG, H_IMG, replica_seed(0))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+
+    if args.only == "fed":
+        k = kaze.Kaze(W_IMG, H_IMG, octaves=OCTAVES, sublevels=SUBLEVELS)
+        x = torch.from_numpy(img).cuda()
+        k.detect(x)
+        st = k.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            k.detect(x)
+            e1.record(st)
+        torch.cuda.synchronize()
+        aos_ms = e0.elapsed_time(e1)
+        k.close()
+        out = run_fed(args, kaze, torch, img, flush, max_over_ranks, barrier, aos_ms)
+    else:
+        k = kaze.Kaze(W_IMG, H_IMG, octaves=OCTAVES, sublevels=SUBLEVELS)
+        x = torch.from_numpy(img).cuda()
+        out = run_describe(args, k, torch, k.stream, flush, k.detect(x), max_over_ranks, barrier)
+        k.close()
+    print(json.dumps({"section": args.only, "workload": WORKLOAD, **out}), flush=True)
+    return 0
+
+
 def run_describe(args, k, torch, stream, flush, kp, max_over_ranks, barrier):
     """Orientation + 64-D M-SURF descriptor (Sec. II-C) of the workload
     image's keypoints on its device-resident levels: one launch per step, the
@@ -582,6 +619,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--only", choices=["describe", "fed"], default=None,
+                    help="run one side section alone on the workload image (profiling cases)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = env_int("RANK", 0)
@@ -589,6 +628,8 @@ def main():
     local_rank = env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only:
+        return run_only(args, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 
