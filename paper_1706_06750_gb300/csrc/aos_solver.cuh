@@ -596,7 +596,10 @@ cudaError_t launch_rows_m(const RowsArgs& a)
 template <int M, int NW>
 cudaError_t launch_cols_m(const ColsArgs& a)
 {
-    if (a.cols == 8)
+    if (a.cols == 16)
+        k_aos_cols<16, M, NW><<<(a.w + 15) / 16, 16 * 32 * NW, a.smem, a.st>>>(a.mL, a.mG, a.ux, a.Lnext, a.pitch,
+                                                                              a.w, a.h, a.tau, a.status);
+    else if (a.cols == 8)
         k_aos_cols<8, M, NW><<<(a.w + 7) / 8, 8 * 32 * NW, a.smem, a.st>>>(a.mL, a.mG, a.ux, a.Lnext, a.pitch,
                                                                            a.w, a.h, a.tau, a.status);
     else
@@ -609,6 +612,7 @@ template <int M, int NW>
 cudaError_t configure_m()
 {
     cudaError_t e = allow_max_dynamic_smem(k_aos_rows<M, NW>);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(k_aos_cols<16, M, NW>);
     if (e == cudaSuccess) e = allow_max_dynamic_smem(k_aos_cols<8, M, NW>);
     if (e == cudaSuccess) e = allow_max_dynamic_smem(k_aos_cols<4, M, NW>);
     return e;

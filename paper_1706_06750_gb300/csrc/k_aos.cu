@@ -15,6 +15,7 @@ KZ_AOS_VARIANTS(KZ_AOS_DECLARE)
 namespace {
 
 constexpr size_t kSmemBudget = 220 * 1024;
+int g_cols_pref = 16;  // widest column strip tried first
 
 size_t row_smem(int w)
 {
@@ -36,6 +37,7 @@ size_t cols_smem(int h, int cols)
 int cols_per_cta(int h)
 {
     if (aos::chunk_len(h) == 0) return 0;
+    if (g_cols_pref == 16 && cols_smem(h, 16) <= kSmemBudget) return 16;
     if (cols_smem(h, 8) <= kSmemBudget) return 8;
     if (cols_smem(h, 4) <= kSmemBudget) return 4;
     return 0;
@@ -129,7 +131,7 @@ cudaError_t launch_aos_cols(const float* L, const float* g, const float* ux, flo
                             float tau, int* d_status, cudaStream_t st, int cols)
 {
     const int c = cols == 0 ? cols_per_cta(h) : cols;
-    if (c == 0 || (c != 4 && c != 8) || cols_smem(h, c) > kSmemBudget) return cudaErrorInvalidValue;
+    if (c == 0 || (c != 4 && c != 8 && c != 16) || cols_smem(h, c) > kSmemBudget) return cudaErrorInvalidValue;
     aos::ColsArgs args;
     if (!make_strip_map(&args.mL, L, pitch, w, h, c) || !make_strip_map(&args.mG, g, pitch, w, h, c))
         return cudaErrorInvalidValue;
