@@ -53,20 +53,22 @@ k_doh(const float* __restrict__ L, float* __restrict__ D, int pitch, long long p
     // lattice rows k0 - 2 .. k0 + WK + 1 of residue py: loads run DPD rows
     // ahead of the filters; the last five filtered rows stay in registers
     constexpr int NM = WK + 4;
+    // element offsets within the level plane fit 32 bits: loads and the
+    // store index from one 64-bit base each
     float buf[DPD + 1][5];
 #pragma unroll
     for (int m = 0; m < DPD; ++m) {
-        const float* row = L + (size_t)reflect_index(py + s * (k0 + m - 2), h) * pitch;
+        const int ro = reflect_index(py + s * (k0 + m - 2), h) * pitch;
 #pragma unroll
-        for (int a = 0; a < 5; ++a) buf[m][a] = __ldg(row + cx[a]);
+        for (int a = 0; a < 5; ++a) buf[m][a] = __ldg(L + (unsigned)(ro + cx[a]));
     }
     float hd[5], hs[5], hx[5];
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         if (m + DPD < NM) {
-            const float* row = L + (size_t)reflect_index(py + s * (k0 + m + DPD - 2), h) * pitch;
+            const int ro = reflect_index(py + s * (k0 + m + DPD - 2), h) * pitch;
 #pragma unroll
-            for (int a = 0; a < 5; ++a) buf[(m + DPD) % (DPD + 1)][a] = __ldg(row + cx[a]);
+            for (int a = 0; a < 5; ++a) buf[(m + DPD) % (DPD + 1)][a] = __ldg(L + (unsigned)(ro + cx[a]));
         }
         const float* v = buf[m % (DPD + 1)];
 #pragma unroll
@@ -79,7 +81,7 @@ k_doh(const float* __restrict__ L, float* __restrict__ D, int pitch, long long p
         if (m < 4) continue;
         const int y = py + s * (k0 + m - 4);
         if (y >= h) break;
-        D[(size_t)y * pitch + x] = doh_value(hd, hs, hx, scale);
+        D[(unsigned)(y * pitch + x)] = doh_value(hd, hs, hx, scale);
     }
 }
 
