@@ -126,18 +126,18 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, float* __restrict
     float pre[GPD + 1][2];
 #pragma unroll
     for (int i = 0; i < GPD && i < NI; ++i) {
-        const float* row = L + (size_t)reflect_index(y0 - 1 - R + i, h) * pitch;
-        pre[i][0] = __ldg(row + c0);
-        pre[i][1] = has1 ? __ldg(row + c1) : 0.f;
+        const int ro = reflect_index(y0 - 1 - R + i, h) * pitch;  // plane offsets fit 32 bits
+        pre[i][0] = __ldg(L + (unsigned)(ro + c0));
+        pre[i][1] = has1 ? __ldg(L + (unsigned)(ro + c1)) : 0.f;
     }
     float hw[2 * R + 1];      // last 2R + 1 horizontally filtered rows
     float dm = 0.f, d0 = 0.f, em = 0.f, e0 = 0.f;  // D, E of the two previous S rows
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
         if (i + GPD < NI) {
-            const float* row = L + (size_t)reflect_index(y0 - 1 - R + i + GPD, h) * pitch;
-            pre[(i + GPD) % (GPD + 1)][0] = __ldg(row + c0);
-            pre[(i + GPD) % (GPD + 1)][1] = has1 ? __ldg(row + c1) : 0.f;
+            const int ro = reflect_index(y0 - 1 - R + i + GPD, h) * pitch;
+            pre[(i + GPD) % (GPD + 1)][0] = __ldg(L + (unsigned)(ro + c0));
+            pre[(i + GPD) % (GPD + 1)][1] = has1 ? __ldg(L + (unsigned)(ro + c1)) : 0.f;
         }
         float* sr_ = srow[warp][i & 1];
         sr_[lane] = pre[i % (GPD + 1)][0];
@@ -170,8 +170,9 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, float* __restrict
             if (out_col && y < h) {
                 if (MODE == MODE_COND) {
                     const float qv = m2 * inv_k2;
-                    g[(size_t)y * pitch + x] = diffusivity == KAZE_G1 ? expf(-qv) : __fdividef(1.f, 1.f + qv);
-                    if (zero) zero[(size_t)y * pitch + x] = 0.f;
+                    const unsigned o = (unsigned)(y * pitch + x);
+                    g[o] = diffusivity == KAZE_G1 ? expf(-qv) : __fdividef(1.f, 1.f + qv);
+                    if (zero) zero[o] = 0.f;
                 } else if (x >= 1 && x <= w - 2 && y >= 1 && y <= h - 2) {
                     const float m = sqrtf(m2);
                     if (MODE == MODE_MAX) {
