@@ -450,16 +450,17 @@ __global__ void __launch_bounds__(128) k_aos_rows(const float* __restrict__ L, c
 template <int COLS, int M, int NW>
 __global__ void __launch_bounds__(COLS * 32 * NW)
     k_aos_cols(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmG,
-               const float* __restrict__ ux, float* __restrict__ Lnext, int pitch, int w, int h, float tau,
-               int* __restrict__ status)
+               const float* __restrict__ gsrc, const float* __restrict__ ux, float* __restrict__ Lnext, int pitch,
+               int w, int h, float tau, int* __restrict__ status)
 {
     constexpr int P = 32 * NW;
     constexpr int NT = COLS * P;
     constexpr int RS = rows_staged(P, M);
     constexpr int V = COLS / 4;                  // float4 per strip row
     constexpr int EPI = (RS * V + NT - 1) / NT;  // epilogue vectors per thread
+    constexpr int NB = RS / 256;  // 256-row boxes, one barrier each
     extern __shared__ __align__(128) float sm[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bars[NB];
     const int tid = threadIdx.x;
     const int c = tid % COLS, p = tid / COLS;
     const int x0 = blockIdx.x * COLS;
@@ -469,28 +470,36 @@ __global__ void __launch_bounds__(COLS * 32 * NW)
     float* eqc = eq0 + (size_t)c * 8 * P;  // this column's equations
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
-        constexpr int NB = RS / 256;
-        mbar_expect_tx(&bar, 2u * NB * 256u * COLS * 4u);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) mbar_init(&bars[b], 1);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            tma_load_2d(tg + (size_t)b * 256 * COLS, &tmG, x0, 256 * b, &bar);
-            tma_load_2d(td + (size_t)b * 256 * COLS, &tmL, x0, 256 * b, &bar);
+            mbar_expect_tx(&bars[b], 2u * 256u * COLS * 4u);
+            tma_load_2d(tg + (size_t)b * 256 * COLS, &tmG, x0, 256 * b, &bars[b]);
+            tma_load_2d(td + (size_t)b * 256 * COLS, &tmL, x0, 256 * b, &bars[b]);
         }
     }
     __syncthreads();
-    const bool ok = mbar_wait_bounded(&bar, 0);
-    if (!__syncthreads_and(ok)) {  // same decision in every thread
-        if (tid == 0) atomicOr(status, 1);
-        return;
-    }
-
+    // a chunk starts as soon as the boxes holding its rows (and the row on
+    // either side) have landed, while later boxes are still in flight
     const int j0 = p * M;
+    bool ok = true;
+    {
+        const int b_lo = (j0 > 0 ? j0 - 1 : 0) / 256;
+        const int b_hi = min(j0 + M, RS - 1) / 256;
+        for (int b = b_lo; b <= b_hi && ok; ++b) ok = mbar_wait_bounded(&bars[b], 0);
+    }
+    if (!__all_sync(FULL, ok)) {  // a wait ran out: every warp still meets the barriers below
+        if ((tid & 31) == 0) atomicOr(status, 1);
+    }
     float* ce = tg + (size_t)j0 * COLS + c;
     float* cd = td + (size_t)j0 * COLS + c;
-    const float g_prev = (j0 > 0 && j0 - 1 < h) ? ce[-COLS] : 0.f;
-    const float g_next = (j0 + M < h) ? ce[M * COLS] : 0.f;
-    __syncthreads();
+    // the neighbouring chunks' edge conductances come from global memory (L2):
+    // their shared copies are overwritten by those chunks' own sweeps, which
+    // no block-wide barrier orders against this read
+    const int xc = x0 + c;
+    const float g_prev = (j0 > 0 && j0 - 1 < h && xc < w) ? __ldg(gsrc + (unsigned)((j0 - 1) * pitch + xc)) : 0.f;
+    const float g_next = (j0 + M < h && xc < w) ? __ldg(gsrc + (unsigned)((j0 + M) * pitch + xc)) : 0.f;
     float ap[M];
     const ChunkEqs q = chunk_reduce<COLS, M>(ce, cd, g_prev, g_next, j0, h, tau, ap);
     eqc[0 * P + p] = q.aL;
@@ -514,7 +523,7 @@ __global__ void __launch_bounds__(COLS * 32 * NW)
     if (ux == nullptr) {
         for (int e = tid; e < h * V; e += NT) {
             const int j = e / V, qq = e - j * V;
-            const size_t gi = (size_t)j * pitch + x0 + 4 * qq;
+            const unsigned gi = (unsigned)(j * pitch + x0 + 4 * qq);  // plane offsets fit 32 bits
             const float* uy = td + (size_t)j * COLS + 4 * qq;
             if (full) {
                 atomicAdd(reinterpret_cast<float4*>(Lnext + gi),
@@ -574,6 +583,7 @@ struct RowsArgs {
 
 struct ColsArgs {
     CUtensorMap mL, mG;
+    const float* g;
     const float* ux;
     float* Lnext;
     int pitch, w, h;
@@ -597,14 +607,14 @@ template <int M, int NW>
 cudaError_t launch_cols_m(const ColsArgs& a)
 {
     if (a.cols == 16)
-        k_aos_cols<16, M, NW><<<(a.w + 15) / 16, 16 * 32 * NW, a.smem, a.st>>>(a.mL, a.mG, a.ux, a.Lnext, a.pitch,
-                                                                              a.w, a.h, a.tau, a.status);
+        k_aos_cols<16, M, NW><<<(a.w + 15) / 16, 16 * 32 * NW, a.smem, a.st>>>(a.mL, a.mG, a.g, a.ux, a.Lnext,
+                                                                              a.pitch, a.w, a.h, a.tau, a.status);
     else if (a.cols == 8)
-        k_aos_cols<8, M, NW><<<(a.w + 7) / 8, 8 * 32 * NW, a.smem, a.st>>>(a.mL, a.mG, a.ux, a.Lnext, a.pitch,
-                                                                           a.w, a.h, a.tau, a.status);
+        k_aos_cols<8, M, NW><<<(a.w + 7) / 8, 8 * 32 * NW, a.smem, a.st>>>(a.mL, a.mG, a.g, a.ux, a.Lnext,
+                                                                           a.pitch, a.w, a.h, a.tau, a.status);
     else
-        k_aos_cols<4, M, NW><<<(a.w + 3) / 4, 4 * 32 * NW, a.smem, a.st>>>(a.mL, a.mG, a.ux, a.Lnext, a.pitch,
-                                                                           a.w, a.h, a.tau, a.status);
+        k_aos_cols<4, M, NW><<<(a.w + 3) / 4, 4 * 32 * NW, a.smem, a.st>>>(a.mL, a.mG, a.g, a.ux, a.Lnext,
+                                                                           a.pitch, a.w, a.h, a.tau, a.status);
     return cudaGetLastError();
 }
 

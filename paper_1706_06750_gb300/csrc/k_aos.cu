@@ -136,6 +136,7 @@ cudaError_t launch_aos_cols(const float* L, const float* g, const float* ux, flo
     if (!make_strip_map(&args.mL, L, pitch, w, h, c) || !make_strip_map(&args.mG, g, pitch, w, h, c))
         return cudaErrorInvalidValue;
     if (!ux && ((pitch & 3) != 0 || ((uintptr_t)Lnext & 15) != 0)) return cudaErrorInvalidValue;
+    args.g = g;
     args.ux = ux;
     args.Lnext = Lnext;
     args.pitch = pitch;
