@@ -159,8 +159,9 @@ __device__ void gradient_tile(int mode, const float* __restrict__ L, float* __re
         const float m2 = fmaf(ly, ly, lx * lx);
         if (gx >= w || gy >= h) continue;
         if (mode == GM_COND) {
-            const float q = m2 * inv_k2;
-            g[(size_t)gy * pitch + gx] = diffusivity == KAZE_G1 ? expf(-q) : __fdividef(1.f, 1.f + q);
+            // explicit fmaf: the single-image kernels write the same operations
+            g[(size_t)gy * pitch + gx] =
+                diffusivity == KAZE_G1 ? expf(-(m2 * inv_k2)) : __fdividef(1.f, fmaf(m2, inv_k2, 1.f));
         } else if (gx >= 1 && gx <= w - 2 && gy >= 1 && gy <= h - 2) {
             const float m = sqrtf(m2);
             if (mode == GM_MAX) {

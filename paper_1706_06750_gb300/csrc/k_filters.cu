@@ -169,18 +169,22 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, float* __restrict
             const float m2 = fmaf(ly, ly, lx * lx);
             if (out_col && y < h) {
                 if (MODE == MODE_COND) {
-                    const float qv = m2 * inv_k2;
                     const unsigned o = (unsigned)(y * pitch + x);
-                    g[o] = diffusivity == KAZE_G1 ? expf(-qv) : __fdividef(1.f, 1.f + qv);
+                    g[o] = diffusivity == KAZE_G1 ? expf(-(m2 * inv_k2)) : __fdividef(1.f, fmaf(m2, inv_k2, 1.f));
                     if (zero) zero[o] = 0.f;
-                } else if (x >= 1 && x <= w - 2 && y >= 1 && y <= h - 2) {
-                    const float m = sqrtf(m2);
-                    if (MODE == MODE_MAX) {
-                        local_max = fmaxf(local_max, m);
-                    } else if (m > 0.f) {
-                        int b = (int)floorf(m * hmax_scale);
-                        b = min(b, nbins - 1);
-                        atomicAdd(&hist_s[b], 1u);
+                } else {
+                    // the max pass may keep |grad|^2 for the histogram and the
+                    // first conductance (g is then an m2 plane)
+                    if (MODE == MODE_MAX && g) g[(unsigned)(y * pitch + x)] = m2;
+                    if (x >= 1 && x <= w - 2 && y >= 1 && y <= h - 2) {
+                        const float m = sqrtf(m2);
+                        if (MODE == MODE_MAX) {
+                            local_max = fmaxf(local_max, m);
+                        } else if (m > 0.f) {
+                            int b = (int)floorf(m * hmax_scale);
+                            b = min(b, nbins - 1);
+                            atomicAdd(&hist_s[b], 1u);
+                        }
                     }
                 }
             }
@@ -248,6 +252,69 @@ __global__ void k_percentile(const unsigned int* __restrict__ hist, int nbins,
 
 __global__ void k_set_scalar(float* d, float v) { *d = v; }
 
+// Histogram pass from the |grad|^2 plane the max pass kept: interior
+// pixels, the same binning as k_gradient<MODE_HIST>.  Four pixels a thread.
+__global__ void __launch_bounds__(256)
+k_hist_m2(const float* __restrict__ m2p, int pitch, int w, int h, const unsigned int* __restrict__ d_hmax_bits,
+          unsigned int* __restrict__ d_hist, int nbins)
+{
+    extern __shared__ unsigned int hist_s[];
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) hist_s[i] = 0u;
+    __syncthreads();
+    const float hmax_scale = (float)nbins / __uint_as_float(*d_hmax_bits);
+    const int y = blockIdx.y;
+    const int x4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (y >= 1 && y <= h - 2 && x4 < w) {
+        const float4 v4 = __ldg(reinterpret_cast<const float4*>(m2p + (unsigned)(y * pitch + x4)));
+        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int x = x4 + q;
+            if (x < 1 || x > w - 2) continue;
+            const float m = sqrtf(v[q]);
+            if (m > 0.f) {
+                int b = (int)floorf(m * hmax_scale);
+                b = min(b, nbins - 1);
+                atomicAdd(&hist_s[b], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
+        const unsigned int c = hist_s[i];
+        if (c) atomicAdd(&d_hist[i], c);
+    }
+}
+
+// Conductance of Eq. 3 from the |grad|^2 plane, in place (the arithmetic of
+// k_gradient<MODE_COND>), zeroing `zero` at the same pixels if given.
+__global__ void __launch_bounds__(256)
+k_cond_m2(float* __restrict__ gm, float* __restrict__ zero, int pitch, int w, int h, const float* __restrict__ d_k,
+          int diffusivity)
+{
+    const float kk = *d_k;
+    const float inv_k2 = 1.f / (kk * kk);
+    const int y = blockIdx.y;
+    const int x4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (y >= h || x4 >= w) return;
+    const unsigned o = (unsigned)(y * pitch + x4);
+    float4 v = *reinterpret_cast<const float4*>(gm + o);
+    float* c = &v.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        c[q] = diffusivity == KAZE_G1 ? expf(-(c[q] * inv_k2)) : __fdividef(1.f, fmaf(c[q], inv_k2, 1.f));
+    }
+    if (x4 + 4 <= w) {
+        *reinterpret_cast<float4*>(gm + o) = v;
+        if (zero) *reinterpret_cast<float4*>(zero + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        for (int q = 0; q < 4 && x4 + q < w; ++q) {
+            gm[o + q] = c[q];
+            if (zero) zero[o + q] = 0.f;
+        }
+    }
+}
+
 template <int MODE, int R>
 cudaError_t launch_gradient_r(const float* L, float* g, float* zero, int pitch, int w, int h, const GaussTaps& taps,
                               const float* d_k, int diffusivity, unsigned int* hmax_bits, unsigned int* hist,
@@ -312,9 +379,29 @@ cudaError_t launch_conductance(const float* L, float* g, float* zero_out, int pi
 }
 
 cudaError_t launch_grad_max(const float* L, int pitch, int w, int h, const GaussTaps& taps,
-                            unsigned int* d_hmax_bits, cudaStream_t st)
+                            unsigned int* d_hmax_bits, cudaStream_t st, float* m2_out)
 {
-    return launch_gradient<MODE_MAX>(L, nullptr, nullptr, pitch, w, h, taps, nullptr, 0, d_hmax_bits, nullptr, 0, st);
+    return launch_gradient<MODE_MAX>(L, m2_out, nullptr, pitch, w, h, taps, nullptr, 0, d_hmax_bits, nullptr, 0, st);
+}
+
+cudaError_t launch_hist_m2(const float* m2, int pitch, int w, int h, const unsigned int* d_hmax_bits,
+                           unsigned int* d_hist, int nbins, cudaStream_t st)
+{
+    if ((pitch & 3) || ((uintptr_t)m2 & 15)) return cudaErrorInvalidValue;
+    const int tx = (w + 3) / 4;
+    dim3 grid((tx + 255) / 256, h);
+    k_hist_m2<<<grid, 256, (size_t)nbins * sizeof(unsigned int), st>>>(m2, pitch, w, h, d_hmax_bits, d_hist, nbins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cond_m2(float* gm, float* zero_out, int pitch, int w, int h, const float* d_k, int diffusivity,
+                           cudaStream_t st)
+{
+    if ((pitch & 3) || (((uintptr_t)gm | (uintptr_t)zero_out) & 15)) return cudaErrorInvalidValue;
+    const int tx = (w + 3) / 4;
+    dim3 grid((tx + 255) / 256, h);
+    k_cond_m2<<<grid, 256, 0, st>>>(gm, zero_out, pitch, w, h, d_k, diffusivity);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_grad_hist(const float* L, int pitch, int w, int h, const GaussTaps& taps,

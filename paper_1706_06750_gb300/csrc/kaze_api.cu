@@ -204,8 +204,10 @@ void set_geometry(kaze_handle* h, int w, int hh)
 float* level_ptr(kaze_handle* h, int i) { return h->levels + (size_t)i * h->cur_plane; }
 float* doh_ptr(kaze_handle* h, int i) { return h->doh + (size_t)i * h->cur_plane; }
 
-// Contrast factor k of the base image into h->d_k (device only).
-kaze_status enqueue_contrast(kaze_handle* h, const float* L0, int pitch, int w, int hh)
+// Contrast factor k of the base image into h->d_k (device only).  With
+// m2_out (a plane of the handle's pitch) the max pass keeps |grad|^2 there
+// and the histogram is taken from it instead of recomputing the gradient.
+kaze_status enqueue_contrast(kaze_handle* h, const float* L0, int pitch, int w, int hh, float* m2_out = nullptr)
 {
     cudaStream_t st = h->stream;
     if (h->opt.k_override > 0.f) {
@@ -214,8 +216,12 @@ kaze_status enqueue_contrast(kaze_handle* h, const float* L0, int pitch, int w, 
     }
     KZ_TRY(h, cudaMemsetAsync(h->d_hmax, 0, sizeof(unsigned int), st));
     KZ_TRY(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned int) * h->opt.nbins, st));
-    KZ_LAUNCH(h, KK_GRAD_MAX, kz::launch_grad_max(L0, pitch, w, hh, h->tapsd, h->d_hmax, st));
-    KZ_LAUNCH(h, KK_GRAD_HIST, kz::launch_grad_hist(L0, pitch, w, hh, h->tapsd, h->d_hmax, h->d_hist, h->opt.nbins, st));
+    KZ_LAUNCH(h, KK_GRAD_MAX, kz::launch_grad_max(L0, pitch, w, hh, h->tapsd, h->d_hmax, st, m2_out));
+    if (m2_out)
+        KZ_LAUNCH(h, KK_GRAD_HIST, kz::launch_hist_m2(m2_out, pitch, w, hh, h->d_hmax, h->d_hist, h->opt.nbins, st));
+    else
+        KZ_LAUNCH(h, KK_GRAD_HIST,
+                  kz::launch_grad_hist(L0, pitch, w, hh, h->tapsd, h->d_hmax, h->d_hist, h->opt.nbins, st));
     KZ_LAUNCH(h, KK_PERCENTILE, kz::launch_percentile(h->d_hist, h->opt.nbins, h->d_hmax, h->opt.k_percentile, h->d_k, st));
     return KAZE_OK;
 }
@@ -228,14 +234,24 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
     const int P = h->cur_pitch;
     KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
     KZ_LAUNCH(h, KK_PRESMOOTH, kz::launch_gaussian(d_img, pitch_elems, level_ptr(h, 0), P, w, hh, h->taps0, st));
-    KZ_CHECK(enqueue_contrast(h, level_ptr(h, 0), P, w, hh));
+    // with k measured here, |grad(G * L_0)|^2 stays in the conductance plane
+    // and the first conductance is computed from it
+    const bool m2 = h->opt.k_override <= 0.f;
+    KZ_CHECK(enqueue_contrast(h, level_ptr(h, 0), P, w, hh, m2 ? h->g : nullptr));
+    auto conductance = [&](int i, const float* Lp, float* zero) -> kaze_status {
+        if (i == 1 && m2)
+            KZ_LAUNCH(h, KK_CONDUCTANCE, kz::launch_cond_m2(h->g, zero, P, w, hh, h->d_k, h->opt.diffusivity, st));
+        else
+            KZ_LAUNCH(h, KK_CONDUCTANCE,
+                      kz::launch_conductance(Lp, h->g, zero, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
+        return KAZE_OK;
+    };
     for (int i = 1; i < h->N; ++i) {
         const float* Lp = level_ptr(h, i - 1);
         float* Li = level_ptr(h, i);
         const float tau = (float)(h->t[i] - h->t[i - 1]);
         if (h->surrogate) {
-            KZ_LAUNCH(h, KK_CONDUCTANCE,
-                      kz::launch_conductance(Lp, h->g, nullptr, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
+            KZ_CHECK(conductance(i, Lp, nullptr));
             kz::sg::Samples S;
             std::memset(&S, 0, sizeof(S));
             S.L[0] = Lp;
@@ -253,8 +269,7 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
         if (h->opt.scheme == KAZE_SCHEME_FED) {
             // one FED cycle: n explicit steps from L_{i-1}, alternating between
             // the row-solution scratch plane and L_i so that the last lands in L_i
-            KZ_LAUNCH(h, KK_CONDUCTANCE,
-                      kz::launch_conductance(Lp, h->g, nullptr, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
+            KZ_CHECK(conductance(i, Lp, nullptr));
             const std::vector<float>& tj = h->fed_tau[i];
             const int n = (int)tj.size();
             const float* src = Lp;
@@ -268,8 +283,7 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
         // conductance also zeroes L_i; the row and column halves of the AOS
         // step then add into it, concurrently on two streams (one stream
         // while profiling, so that events bracket single kernels)
-        KZ_LAUNCH(h, KK_CONDUCTANCE,
-                  kz::launch_conductance(Lp, h->g, Li, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
+        KZ_CHECK(conductance(i, Lp, Li));
         const bool fork = !h->profiling && h->side != nullptr;
         if (fork) {
             KZ_TRY(h, cudaEventRecord(h->ev_fork, st));

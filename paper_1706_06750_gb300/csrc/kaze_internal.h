@@ -108,8 +108,16 @@ cudaError_t launch_conductance(const float* L, float* g, float* zero_out, int pi
 
 // Contrast factor: hmax pass, histogram pass, percentile pick.  hmax is kept
 // as the bit pattern of a non-negative float (ordered like an unsigned int).
+// m2_out (optional): receives |grad|^2 of every pixel, for launch_hist_m2
+// and launch_cond_m2 (the same values the gradient kernels compute).
 cudaError_t launch_grad_max(const float* L, int pitch, int w, int h, const GaussTaps& taps,
-                            unsigned int* d_hmax_bits, cudaStream_t st);
+                            unsigned int* d_hmax_bits, cudaStream_t st, float* m2_out = nullptr);
+// The histogram pass and the conductance (in place, zeroing zero_out) from
+// such a plane; rows 16-byte aligned, pitch % 4 == 0.
+cudaError_t launch_hist_m2(const float* m2, int pitch, int w, int h, const unsigned int* d_hmax_bits,
+                           unsigned int* d_hist, int nbins, cudaStream_t st);
+cudaError_t launch_cond_m2(float* gm, float* zero_out, int pitch, int w, int h, const float* d_k, int diffusivity,
+                           cudaStream_t st);
 cudaError_t launch_grad_hist(const float* L, int pitch, int w, int h, const GaussTaps& taps,
                              const unsigned int* d_hmax_bits, unsigned int* d_hist, int nbins,
                              cudaStream_t st);
