@@ -308,7 +308,7 @@ def test_invalid_arguments(K):
 
 def test_trained_surrogate_against_aos(K, capsys):
     """What the committed, trained network gains over the method without it
-    (plain GPU AOS, the judge) on two held-out 1920x1200 workload images:
+    (measured against plain GPU AOS) on two held-out 1920x1200 workload images:
     it reproduces most of each early AOS step and keeps most AOS keypoints,
     and it costs more time than the step it replaces.  The numbers are
     printed; the asserts hold the trained checkpoint to what it measured
