@@ -395,9 +395,12 @@ k_surrogate_tc(const __nv_bfloat16* __restrict__ wpad, const float* __restrict__
                                     const float s1 = __shfl_up_sync(0xffffffffu, __uint_as_float(v[c + 1]), 1) +
                                                      __uint_as_float(v[17 + c]) +
                                                      __shfl_down_sync(0xffffffffu, __uint_as_float(v[33 + c]), 1);
-                                    const float a0 = inside ? fmaxf(s0 + bb[16 * hf + c], 0.f) : 0.f;
-                                    const float a1 = inside ? fmaxf(s1 + bb[16 * hf + c + 1], 0.f) : 0.f;
-                                    ow[j] = pack_bf16x2(a0, a1);
+                                    // ReLU after the BF16 rounding (the same values: rounding
+                                    // keeps signs), one select per packed pair
+                                    __nv_bfloat162 pr = __floats2bfloat162_rn(s0 + bb[16 * hf + c],
+                                                                              s1 + bb[16 * hf + c + 1]);
+                                    pr = __hmax2(pr, __floats2bfloat162_rn(0.f, 0.f));
+                                    ow[j] = inside ? *reinterpret_cast<uint32_t*>(&pr) : 0u;
                                 }
                                 dst[(2 * hf + gq) * TC_BP + TC_FS + p] = o;
                             }
