@@ -119,14 +119,15 @@ class ClockSampler:
 
 def algorithmic_bytes(kind, pixels, n_levels, nbins=300):
     """Minimum bytes a kernel kind must move in one detection (FP32 planes):
-    presmoothing reads I and writes L_0; the contrast passes read L_0; each of
+    presmoothing reads I and writes L_0; the max pass reads L_0 and keeps
+    |grad|^2, which the histogram pass reads; each of
     the N-1 steps writes g (read L), then its row and column halves each read
     L and g and write (add) their half of L_i; the response reads and writes
     every level, the extrema read every response once."""
     steps = n_levels - 1
     # the AOS halves each read L and g and add half of L_i
     table = {
-        "presmooth": 8, "grad_max": 4, "grad_hist": 4, "conductance": 8 * steps,
+        "presmooth": 8, "grad_max": 8, "grad_hist": 4, "conductance": 8 * steps,
         "aos_rows": 12 * steps, "aos_cols": 12 * steps, "doh": 8 * n_levels, "extrema": 4 * n_levels,
     }
     if kind in table:
