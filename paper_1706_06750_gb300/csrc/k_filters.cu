@@ -212,11 +212,9 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, float* __restrict
 // slice sums are prefix-summed with shuffles, and the lane whose slice
 // crosses pct * n walks its bins.  k = hmax * (b + 1) / nbins; 0.03 when no
 // pixel was binned.
-__global__ void k_percentile(const unsigned int* __restrict__ hist, int nbins,
-                             const unsigned int* __restrict__ d_hmax_bits, double pct,
-                             float* __restrict__ d_k)
+__device__ __forceinline__ void percentile_pick(const unsigned int* hist, int nbins,
+                                                const unsigned int* d_hmax_bits, double pct, float* d_k, int lane)
 {
-    const int lane = threadIdx.x;
     const int per = (nbins + 31) / 32;
     const int b0 = min(lane * per, nbins), b1 = min(b0 + per, nbins);
     unsigned long long s = 0;
@@ -250,14 +248,22 @@ __global__ void k_percentile(const unsigned int* __restrict__ hist, int nbins,
     }
 }
 
+__global__ void k_percentile(const unsigned int* __restrict__ hist, int nbins,
+                             const unsigned int* __restrict__ d_hmax_bits, double pct,
+                             float* __restrict__ d_k)
+{
+    percentile_pick(hist, nbins, d_hmax_bits, pct, d_k, threadIdx.x);
+}
+
 __global__ void k_set_scalar(float* d, float v) { *d = v; }
 
 // Histogram pass from the |grad|^2 plane the max pass kept: interior
 // pixels, the same binning as k_gradient<MODE_HIST>.  Four pixels a thread.
 __global__ void __launch_bounds__(256)
 k_hist_m2(const float* __restrict__ m2p, int pitch, int w, int h, const unsigned int* __restrict__ d_hmax_bits,
-          unsigned int* __restrict__ d_hist, int nbins)
+          unsigned int* __restrict__ d_hist, int nbins, double pct, float* __restrict__ d_k)
 {
+    __shared__ bool s_last;
     extern __shared__ unsigned int hist_s[];
     for (int i = threadIdx.x; i < nbins; i += blockDim.x) hist_s[i] = 0u;
     __syncthreads();
@@ -283,6 +289,17 @@ k_hist_m2(const float* __restrict__ m2p, int pitch, int w, int h, const unsigned
     for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
         const unsigned int c = hist_s[i];
         if (c) atomicAdd(&d_hist[i], c);
+    }
+    // the last block to finish picks the percentile (d_hist[nbins] counts
+    // finished blocks): no separate launch, no block waits for another
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = atomicAdd(&d_hist[nbins], 1u) == gridDim.x * gridDim.y - 1u;
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+        __threadfence();
+        percentile_pick(d_hist, nbins, d_hmax_bits, pct, d_k, threadIdx.x);
     }
 }
 
@@ -385,12 +402,13 @@ cudaError_t launch_grad_max(const float* L, int pitch, int w, int h, const Gauss
 }
 
 cudaError_t launch_hist_m2(const float* m2, int pitch, int w, int h, const unsigned int* d_hmax_bits,
-                           unsigned int* d_hist, int nbins, cudaStream_t st)
+                           unsigned int* d_hist, int nbins, double pct, float* d_k, cudaStream_t st)
 {
     if ((pitch & 3) || ((uintptr_t)m2 & 15)) return cudaErrorInvalidValue;
     const int tx = (w + 3) / 4;
     dim3 grid((tx + 255) / 256, h);
-    k_hist_m2<<<grid, 256, (size_t)nbins * sizeof(unsigned int), st>>>(m2, pitch, w, h, d_hmax_bits, d_hist, nbins);
+    k_hist_m2<<<grid, 256, (size_t)nbins * sizeof(unsigned int), st>>>(m2, pitch, w, h, d_hmax_bits, d_hist, nbins,
+                                                                        pct, d_k);
     return cudaGetLastError();
 }
 

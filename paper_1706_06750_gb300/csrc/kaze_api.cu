@@ -215,14 +215,17 @@ kaze_status enqueue_contrast(kaze_handle* h, const float* L0, int pitch, int w, 
         return KAZE_OK;
     }
     KZ_TRY(h, cudaMemsetAsync(h->d_hmax, 0, sizeof(unsigned int), st));
-    KZ_TRY(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned int) * h->opt.nbins, st));
+    KZ_TRY(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned int) * (h->opt.nbins + 1), st));
     KZ_LAUNCH(h, KK_GRAD_MAX, kz::launch_grad_max(L0, pitch, w, hh, h->tapsd, h->d_hmax, st, m2_out));
-    if (m2_out)
-        KZ_LAUNCH(h, KK_GRAD_HIST, kz::launch_hist_m2(m2_out, pitch, w, hh, h->d_hmax, h->d_hist, h->opt.nbins, st));
-    else
+    if (m2_out) {  // histogram and percentile in one launch
+        KZ_LAUNCH(h, KK_GRAD_HIST, kz::launch_hist_m2(m2_out, pitch, w, hh, h->d_hmax, h->d_hist, h->opt.nbins,
+                                                      h->opt.k_percentile, h->d_k, st));
+    } else {
         KZ_LAUNCH(h, KK_GRAD_HIST,
                   kz::launch_grad_hist(L0, pitch, w, hh, h->tapsd, h->d_hmax, h->d_hist, h->opt.nbins, st));
-    KZ_LAUNCH(h, KK_PERCENTILE, kz::launch_percentile(h->d_hist, h->opt.nbins, h->d_hmax, h->opt.k_percentile, h->d_k, st));
+        KZ_LAUNCH(h, KK_PERCENTILE,
+                  kz::launch_percentile(h->d_hist, h->opt.nbins, h->d_hmax, h->opt.k_percentile, h->d_k, st));
+    }
     return KAZE_OK;
 }
 
@@ -554,7 +557,7 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     const size_t off_stage = bytes;  bytes += al(sizeof(float) * pm);
     const size_t off_k = bytes;      bytes += al(sizeof(float));
     const size_t off_hmax = bytes;   bytes += al(sizeof(unsigned int));
-    const size_t off_hist = bytes;   bytes += al(sizeof(unsigned int) * o.nbins);
+    const size_t off_hist = bytes;   bytes += al(sizeof(unsigned int) * (o.nbins + 1));  // + a block counter
     const size_t off_cnt = bytes;    bytes += al(sizeof(unsigned int));
     const size_t off_status = bytes; bytes += al(sizeof(int));
     const size_t off_kp = bytes;     bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);

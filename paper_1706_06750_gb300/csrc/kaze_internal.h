@@ -114,8 +114,10 @@ cudaError_t launch_grad_max(const float* L, int pitch, int w, int h, const Gauss
                             unsigned int* d_hmax_bits, cudaStream_t st, float* m2_out = nullptr);
 // The histogram pass and the conductance (in place, zeroing zero_out) from
 // such a plane; rows 16-byte aligned, pitch % 4 == 0.
+// launch_hist_m2 also picks the percentile (its last block): d_hist holds
+// nbins + 1 counters, all zero before the launch, and k lands in d_k.
 cudaError_t launch_hist_m2(const float* m2, int pitch, int w, int h, const unsigned int* d_hmax_bits,
-                           unsigned int* d_hist, int nbins, cudaStream_t st);
+                           unsigned int* d_hist, int nbins, double pct, float* d_k, cudaStream_t st);
 cudaError_t launch_cond_m2(float* gm, float* zero_out, int pitch, int w, int h, const float* d_k, int diffusivity,
                            cudaStream_t st);
 cudaError_t launch_grad_hist(const float* L, int pitch, int w, int h, const GaussTaps& taps,
