@@ -460,6 +460,24 @@ void kaze_surrogate_destroy(kaze_surrogate* s);
  * Drops the handle's recorded detection graph. */
 kaze_status kaze_set_surrogate(kaze_handle* h, kaze_surrogate* s);
 
+/* Loads a surrogate checkpoint (the format of kaze_surrogate_save) into a
+ * surrogate the handle owns and evolves the scale space with it from then
+ * on, as kaze_set_surrogate does; path NULL restores AOS and frees it.  A
+ * file that is not a checkpoint gives KAZE_ERR_INVALID_ARG and leaves the
+ * handle as it was.  Synchronises. */
+kaze_status kaze_load_surrogate(kaze_handle* h, const char* path);
+
+/* The whole detection of n images of (possibly different) sizes w[i] x h[i]
+ * (3..4096, rows contiguous: pitch = w[i]) on device memory d_imgs[i], with
+ * the handle's options, through one batch (kaze_batch_create /
+ * kaze_batch_detect, which the handle keeps while the size list repeats).
+ * Image i's keypoints, sorted by (level, iy, ix), go to h_out + i *
+ * capacity and their true number to counts[i]; KAZE_ERR_CAPACITY when one
+ * exceeds capacity.  Batches evolve by AOS and test 3x3x3 maxima.
+ * Synchronises. */
+kaze_status kaze_build_batch(kaze_handle* h, const float* const* d_imgs, const int* w, const int* h_, int n,
+                             kaze_keypoint* h_out, int capacity, int* counts);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Number of kernel kinds the pipeline launches, and the name of kind k

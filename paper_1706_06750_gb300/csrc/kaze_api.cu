@@ -72,8 +72,13 @@ struct kaze_handle {
     kz::GaussTaps taps0, tapsd;
     kz::LevelTable tab;
 
-    // learned stand-in for the AOS step (borrowed; NULL: AOS)
+    // learned stand-in for the AOS step (borrowed; NULL: AOS), and the one
+    // the handle owns when it loaded the checkpoint itself
     const kaze_surrogate* surrogate = nullptr;
+    kaze_surrogate* own_surrogate = nullptr;
+    // the batch kaze_build_batch runs, kept while the image sizes repeat
+    kaze_batch* batch = nullptr;
+    std::vector<int> batch_w, batch_h;
     float sg_s[kz::kMaxLevels];  // BF16 value of log(1 + tau_i) / 5 per level
 
     // recorded detection graph
@@ -917,6 +922,52 @@ KAZE_API kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch
     return collect_keypoints(h, h_out, capacity, count);
 }
 
+KAZE_API kaze_status kaze_load_surrogate(kaze_handle* h, const char* path)
+{
+    if (!h) return KAZE_ERR_INVALID_ARG;
+    if (!path) {  // back to AOS
+        kaze_set_surrogate(h, nullptr);
+        if (h->own_surrogate) kaze_surrogate_destroy(h->own_surrogate);
+        h->own_surrogate = nullptr;
+        return KAZE_OK;
+    }
+    kaze_surrogate* s = nullptr;
+    kaze_status st = kaze_surrogate_create(0, 0, 0, 0, 0ull, (void*)h->stream, &s);
+    if (st != KAZE_OK) return fail(h, st, std::string("kaze_surrogate_create: ") + kaze_surrogate_last_error(nullptr));
+    st = kaze_surrogate_load(s, path);
+    if (st != KAZE_OK) {
+        const std::string msg = std::string("kaze_surrogate_load: ") + kaze_surrogate_last_error(s);
+        kaze_surrogate_destroy(s);
+        return fail(h, st, msg);
+    }
+    kaze_set_surrogate(h, s);
+    if (h->own_surrogate) kaze_surrogate_destroy(h->own_surrogate);
+    h->own_surrogate = s;
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_build_batch(kaze_handle* h, const float* const* d_imgs, const int* w, const int* hh, int n,
+                                      kaze_keypoint* h_out, int capacity, int* counts)
+{
+    if (!h || !d_imgs || !w || !hh || n < 1 || capacity < 0 || (capacity > 0 && !h_out) || !counts)
+        return fail(h, KAZE_ERR_INVALID_ARG, "bad batch arguments");
+    const std::vector<int> ws(w, w + n), hs(hh, hh + n);
+    if (!h->batch || ws != h->batch_w || hs != h->batch_h) {
+        if (h->batch) kaze_batch_destroy(h->batch);
+        h->batch = nullptr;
+        kaze_batch* b = nullptr;
+        const kaze_status st = kaze_batch_create(&h->opt, n, w, hh, (void*)h->stream, &b);
+        if (st != KAZE_OK) return fail(h, st, "kaze_batch_create refused the batch (sizes 3..4096; AOS, 3x3x3 maxima)");
+        h->batch = b;
+        h->batch_w = ws;
+        h->batch_h = hs;
+    }
+    const kaze_status st = kaze_batch_detect(h->batch, d_imgs, nullptr, h_out, capacity, counts);
+    if (st != KAZE_OK && st != KAZE_ERR_CAPACITY)
+        return fail(h, st, std::string("kaze_batch_detect: ") + kaze_batch_last_error(h->batch));
+    return st;
+}
+
 KAZE_API kaze_status kaze_set_surrogate(kaze_handle* h, kaze_surrogate* s)
 {
     if (!h) return KAZE_ERR_INVALID_ARG;
@@ -1017,6 +1068,8 @@ KAZE_API void kaze_destroy(kaze_handle* h)
     if (h->h_count) cudaFreeHost(h->h_count);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->own_surrogate) kaze_surrogate_destroy(h->own_surrogate);
+    if (h->batch) kaze_batch_destroy(h->batch);
     if (h->side) cudaStreamDestroy(h->side);
     delete h;
 }

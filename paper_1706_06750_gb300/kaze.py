@@ -145,6 +145,9 @@ _SIGNATURES = {
     "kaze_kernel_name": (ctypes.c_char_p, [_i]),
     "kaze_last_launch_count": (_i, [_vp]),
     "kaze_profile": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)]),
+    "kaze_load_surrogate": (_i, [_vp, ctypes.c_char_p]),
+    "kaze_build_batch": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _vp, _i,
+                              ctypes.POINTER(_i)]),
     "kaze_op_fed_cycle": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _f, ctypes.POINTER(_i)]),
     "kaze_describe": (_i, [_vp, _vp, _i, _vp, _i]),
     "kaze_describe_device": (_i, [_vp, _vp, _i, _vp, _i]),
@@ -475,6 +478,34 @@ class Kaze:
         self._ck(self._L.kaze_set_surrogate(self._h, surrogate._s if surrogate is not None else None),
                  "kaze_set_surrogate")
         self._surrogate = surrogate
+
+    def load_surrogate(self, path):
+        """Evolve with a surrogate checkpoint the handle loads and owns
+        (None restores AOS)."""
+        self._ck(self._L.kaze_load_surrogate(self._h, None if path is None else os.fsencode(path)),
+                 "kaze_load_surrogate")
+
+    def build_batch(self, imgs, capacity=None):
+        """Detection of a list of 2-D float32 CUDA tensors (contiguous rows)
+        through one batch with the handle's options; a list of keypoint
+        arrays, one per image."""
+        n = len(imgs)
+        for t in imgs:
+            w, h, pitch = _check_image(t)
+            if pitch != w:
+                raise KazeError(ERR_INVALID_ARG, "build_batch needs contiguous rows (pitch == width)")
+        ptrs = (_vp * n)(*[t.data_ptr() for t in imgs])
+        ws = (_i * n)(*[t.shape[1] for t in imgs])
+        hs = (_i * n)(*[t.shape[0] for t in imgs])
+        cap = self.options.max_keypoints if capacity is None else int(capacity)
+        buf = (Keypoint * (cap * n))()
+        counts = (_i * n)()
+        self._begin()
+        st = self._ck(self._L.kaze_build_batch(self._h, ptrs, ws, hs, n, buf, cap, counts), "kaze_build_batch")
+        self._end()
+        self.last_status = st
+        raw = np.frombuffer(buf, dtype=KEYPOINT_DTYPE, count=cap * n)
+        return [raw[i * cap: i * cap + min(counts[i], cap)].copy() for i in range(n)]
 
     def last_launch_count(self):
         return int(self._L.kaze_last_launch_count(self._h))

@@ -137,3 +137,23 @@ def test_mixed_size_workload_sample(kz):
             ref = k.detect(xs[i])
         ov, m, ur, ug, md = compare(ref, kps[i], D[i])
         assert ov >= 0.995 and not ur and not ug, (i, ov, ur[:2], ug[:2])
+
+
+def test_handle_build_batch_equals_batch_object(kz):
+    """kaze_build_batch on a handle runs the same batch as kaze_batch_* and
+    keeps it while the size list repeats."""
+    sizes = SIZES[:3]
+    imgs = images(sizes, 950)
+    xs = [torch.from_numpy(a).cuda() for a in imgs]
+    with kz.Batch(sizes, octaves=2, sublevels=4) as b:
+        ref = b.detect(xs)
+    with kz.Kaze(4096, 4096, octaves=2, sublevels=4) as k:
+        got = k.build_batch(xs)
+        again = k.build_batch(xs)
+        for a, r, g in zip(got, ref, again):
+            assert np.array_equal(a, r) and np.array_equal(g, r)
+        with pytest.raises(kz.KazeError):
+            k.build_batch([torch.zeros((2, 64), device="cuda")])
+    with kz.Kaze(256, 256, scheme=kz.SCHEME_FED) as k:
+        with pytest.raises(kz.KazeError):
+            k.build_batch(xs)

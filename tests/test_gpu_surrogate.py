@@ -339,3 +339,32 @@ def test_trained_surrogate_against_aos(K, capsys):
     # time: both measured; the surrogate is the slower stand-in
     assert r["evolution_ms_aos"] > 0 and r["evolution_ms_surrogate"] > 0
     assert r["batched_step_ms_surrogate"] > r["batched_step_ms_aos"]
+
+
+def test_handle_loads_a_checkpoint(K, tmp_path):
+    """kaze_load_surrogate: the handle's own copy of a checkpoint gives the
+    same detection as a borrowed surrogate holding it; NULL restores AOS;
+    a file that is no checkpoint is refused and changes nothing."""
+    from paper_1706_06750_gb300 import synth
+    ckpt = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_1706_06750_gb300", "weights", "surrogate.ckpt")
+    img = torch.from_numpy(synth.image(160, 128, 31)).cuda()
+    s = K.Surrogate(seed=0)
+    s.load(ckpt)
+    with K.Kaze(160, 128, octaves=2, sublevels=3) as k:
+        plain = k.detect(img)
+        k.set_surrogate(s)
+        borrowed = k.detect(img)
+        L_b = k.levels().cpu().numpy()
+        k.set_surrogate(None)
+        k.load_surrogate(ckpt)
+        owned = k.detect(img)
+        assert np.array_equal(k.levels().cpu().numpy(), L_b) and np.array_equal(owned, borrowed)
+        bad = tmp_path / "not_a_checkpoint.bin"
+        bad.write_bytes(b"nothing here")
+        with pytest.raises(K.KazeError):
+            k.load_surrogate(str(bad))
+        assert np.array_equal(k.detect(img), borrowed)
+        k.load_surrogate(None)
+        assert np.array_equal(k.detect(img), plain)
+    s.close()
