@@ -222,6 +222,46 @@ def oracle_sample_rate(img, seconds_budget, octaves=OCTAVES, sublevels=SUBLEVELS
     return cw * ch / dt / 1e6, cw, ch, dt
 
 
+def _oracle_worker_init():
+    import oracle
+    oracle.build()
+
+
+def _oracle_crop_job(args):
+    crop, octaves, sublevels = args
+    import oracle
+    oracle.kaze_detect(crop, oracle.Options.make(octaves=octaves, sublevels=sublevels))
+    return crop.size
+
+
+def oracle_all_cores_rate(img, seconds_budget, octaves=OCTAVES, sublevels=SUBLEVELS):
+    """The FP64 oracle as it stands on every host core at once: one process
+    per core (spawned), each detecting its own copy of a centred crop; the
+    pool is started before the clock.  Returns (Mpixel/s, cores, crop w,
+    crop h, seconds)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    cores = os.cpu_count() or 1
+    h, w = img.shape
+    sec_per_px = 4e-6
+    area = max(64 * 64, min(w * h, int(seconds_budget / sec_per_px)))
+    scale = min(1.0, (area / (w * h)) ** 0.5)
+    cw, ch = max(32, int(w * scale)), max(32, int(h * scale))
+    x0, y0 = (w - cw) // 2, (h - ch) // 2
+    crop = np.ascontiguousarray(img[y0:y0 + ch, x0:x0 + cw], dtype=np.float64)
+    with mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init) as pool:
+        pool.map(_oracle_worker_init_probe, range(cores))  # every worker is up
+        t0 = time.perf_counter()
+        px = sum(pool.map(_oracle_crop_job, [(crop, octaves, sublevels)] * cores, chunksize=1))
+        dt = time.perf_counter() - t0
+    return px / dt / 1e6, cores, cw, ch, dt
+
+
+def _oracle_worker_init_probe(_):
+    return 0
+
+
 # ------------------------------------------------------------ multi-rank --
 
 def replica_seed(rank):
@@ -387,6 +427,10 @@ def run_ours(args, rank, world, local_rank):
                "sample": f"centred {cw}x{ch} crop of the 1920x1200 workload image, "
                          f"{OCTAVES}x{SUBLEVELS} levels, scale space + response + extrema, "
                          f"FP64 oracle single thread, {secs:.1f} s"}
+        arate, cores, acw, ach, asecs = oracle_all_cores_rate(img, args.cpu_seconds / 2)
+        cpu["all_cores"] = {"value": arate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{cores} processes, each the same centred {acw}x{ach} crop, "
+                                      f"{asecs:.1f} s wall"}
 
     value = whole_job_rate(world, args.steps, pixels, t_dev_ms)
     e2e = whole_job_rate(world, args.steps, pixels, t_e2e_ms)
