@@ -1,7 +1,7 @@
 // k_describe.cu -- keypoint description (Sec. II-C): the dominant orientation
 // and the 64-D M-SURF descriptor of each keypoint on its scale level.
 //
-// One CTA of 256 threads per keypoint; all levels are served by the same
+// One CTA of 512 threads per keypoint; all levels are served by the same
 // launch (the level index comes with the keypoint), so keypoints of every
 // scale are described concurrently.  First derivatives are evaluated where
 // they are needed, from the level itself: the step-s Scharr pair of the
@@ -19,8 +19,8 @@
 // one warp picks the longest window sum (the first on ties), whose angle is
 // the orientation.
 // Descriptor: 16 subregions of 9 x 9 samples (centres 5 sigma_i apart,
-// spacing sigma_i) in the keypoint's rotated frame; 16 threads per
-// subregion accumulate (sum r_x', sum r_y', sum |r_x'|, sum |r_y'|) with the
+// spacing sigma_i) in the keypoint's rotated frame; a warp per subregion
+// accumulates (sum r_x', sum r_y', sum |r_x'|, sum |r_y'|) with the
 // subregion's Gaussian (std 2.5 sigma_i), reduce by shuffles, apply the 4 x
 // 4 mask weight (std 1.5 grid units) and the vector is normalised to unit
 // length.  Every memory access is clamped into its buffer.
@@ -31,7 +31,7 @@
 namespace kz {
 namespace {
 
-constexpr int DT = 256;
+constexpr int DT = 512;
 constexpr int kOriN = 109;
 constexpr int kSectors = 72;
 constexpr int kWindow = 12;
@@ -181,11 +181,12 @@ __global__ void __launch_bounds__(DT) k_describe(const float* __restrict__ level
     float si, co;
     sincosf(theta, &si, &co);
 
-    // descriptor: subregion r = t / 16 (p = r % 4 along x', q = r / 4 along y')
-    const int r = t >> 4, l16 = t & 15;
+    // descriptor: subregion r = t / 32 (p = r % 4 along x', q = r / 4 along y'),
+    // one warp per subregion
+    const int r = t >> 5, l32 = lane;
     const float cp = ((float)(r & 3) - 1.5f) * 5.f, cq = ((float)(r >> 2) - 1.5f) * 5.f;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    for (int j = l16; j < 81; j += 16) {
+    for (int j = l32; j < 81; j += 32) {
         const float du = cp + (float)(j % 9 - 4), dv = cq + (float)(j / 9 - 4);
         const float ox = sigma * fmaf(du, co, -dv * si), oy = sigma * fmaf(du, si, dv * co);
         float gx, gy;
@@ -198,13 +199,13 @@ __global__ void __launch_bounds__(DT) k_describe(const float* __restrict__ level
         a3 = fmaf(w1, fabsf(ryp), a3);
     }
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
+    for (int o = 16; o > 0; o >>= 1) {
         a0 += __shfl_xor_sync(0xffffffffu, a0, o);
         a1 += __shfl_xor_sync(0xffffffffu, a1, o);
         a2 += __shfl_xor_sync(0xffffffffu, a2, o);
         a3 += __shfl_xor_sync(0xffffffffu, a3, o);
     }
-    if (l16 == 0) {
+    if (l32 == 0) {
         const float w2 = c_grid_w[r];
         s_desc[4 * r + 0] = w2 * a0;
         s_desc[4 * r + 1] = w2 * a1;
