@@ -488,13 +488,26 @@ def run_fed(args, kaze, torch, img, flush, max_over_ranks, barrier, aos_ms):
     torch.cuda.synchronize()
     ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / reps)
     prof = k.profile(x)
+    t = [k.level_time(i) for i in range(OCTAVES * SUBLEVELS)]
     k.close()
+    steps = sum(fed_cycle_length(b - a) for a, b in zip(t, t[1:]))
     fed_ms, fed_n = prof.get("fed", (0.0, 0))
+    # a launch takes up to four explicit steps and moves 12 bytes a pixel (read L, g; write L)
     return {"ms_per_step": ms, "mpix_per_s": W_IMG * H_IMG / (ms * 1e-3) / 1e6, "keypoints": n_kp,
-            "launches_per_step": launches, "explicit_steps": fed_n,
-            "ms_per_explicit_step": fed_ms / fed_n if fed_n else None,
-            "explicit_step_algorithmic_gbs": (12 * W_IMG * H_IMG / (fed_ms / fed_n * 1e-3) / 1e9) if fed_n else None,
+            "launches_per_step": launches, "explicit_steps": steps, "fed_launches": fed_n,
+            "ms_per_fed_launch": fed_ms / fed_n if fed_n else None,
+            "ms_per_explicit_step": fed_ms / steps if steps else None,
+            "fed_launch_algorithmic_gbs": (12 * W_IMG * H_IMG / (fed_ms / fed_n * 1e-3) / 1e9) if fed_n else None,
             "aos_ms_per_step": aos_ms, "aos_over_fed_speed": ms / aos_ms}
+
+
+def fed_cycle_length(dt, tau_max=0.25):
+    """Explicit steps of the FED cycle reaching dt: the least n with
+    tau_max (n^2 + n) / 3 >= dt (Eq. 5)."""
+    n = 1
+    while tau_max * (n * n + n) / 3.0 < dt:
+        n += 1
+    return n
 
 
 def run_only(args, local_rank):

@@ -233,12 +233,23 @@ kaze_status kaze_op_aos_step(kaze_handle* h, const float* d_Lprev, const float* 
 
 /* One FED cycle (Eq. 5) from d_Lprev to stopping time dt with the
  * conductance d_g held fixed: n explicit steps of the handle's scheme
- * (fed_tau_max), alternating between d_scratch and d_Lnext and ending in
- * d_Lnext.  All buffers share pitch (a multiple of 4) and start on 16-byte
- * boundaries; outputs must not alias inputs or each other.  *n_steps (may be
- * NULL) receives n.  Async. */
+ * (fed_tau_max), up to four per launch, alternating between d_scratch and
+ * d_Lnext and ending in d_Lnext.  All buffers share pitch (a multiple of 4)
+ * and start on 16-byte boundaries; outputs must not alias inputs or each
+ * other.  *n_steps (may be NULL) receives n.  Synchronises the stream (it
+ * reports a timed-out device wait as KAZE_ERR_TIMEOUT). */
 kaze_status kaze_op_fed_cycle(kaze_handle* h, const float* d_Lprev, const float* d_g, float* d_scratch,
                               float* d_Lnext, int pitch, int w, int h_, float dt, int* n_steps);
+
+/* k explicit steps of Eq. 5 (1 <= k <= 4), of sizes h_tau[0..k-1] in that
+ * order, from d_Lprev into d_Lnext with d_g held fixed, in one launch (the
+ * steps are taken as a wavefront over the rows of tiles staged in shared
+ * memory, with a 4-column halo per warp); the result equals k single steps
+ * bit for bit.  Same layout rules as kaze_op_fed_cycle; d_Lnext may not
+ * alias d_Lprev or d_g.  Synchronises the stream, as kaze_op_fed_cycle
+ * does. */
+kaze_status kaze_op_fed_steps(kaze_handle* h, const float* d_Lprev, const float* d_g, float* d_Lnext,
+                              int pitch, int w, int h_, const float* h_tau, int k);
 
 /* Detector response of Eq. 8 of one level: step s = max(1, round(sigma_i)),
  * normalisation by the handle's doh_norm.  Async. */

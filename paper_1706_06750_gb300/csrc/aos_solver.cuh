@@ -645,4 +645,9 @@ cudaError_t configure_m()
     template cudaError_t configure_m<M, NW>();
 
 }  // namespace aos
+
+// 2-D tensor map of a w x h FP32 plane (row pitch in elements) with a
+// box_x x box_y box; reads past the plane's edges fill with zeros.
+bool make_plane_map(CUtensorMap* map, const float* base, int pitch, int w, int h, int box_x, int box_y);
+
 }  // namespace kz

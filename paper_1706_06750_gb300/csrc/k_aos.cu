@@ -70,14 +70,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return nullptr;
 }
 
-// 2-D map of a w x h FP32 plane with the given pitch, box COLS x 256.
-bool make_strip_map(CUtensorMap* map, const float* base, int pitch, int w, int h, int cols)
+}  // namespace
+
+bool make_plane_map(CUtensorMap* map, const float* base, int pitch, int w, int h, int box_x, int box_y)
 {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
     cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)cols, 256u};
+    cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
     cuuint32_t estr[2] = {1u, 1u};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -85,6 +86,12 @@ bool make_strip_map(CUtensorMap* map, const float* base, int pitch, int w, int h
     return r == CUDA_SUCCESS;
 }
 
+namespace {
+// 2-D map of a w x h FP32 plane with the given pitch, box COLS x 256.
+bool make_strip_map(CUtensorMap* map, const float* base, int pitch, int w, int h, int cols)
+{
+    return make_plane_map(map, base, pitch, w, h, cols, 256);
+}
 }  // namespace
 
 const char* aos_config_error() { return g_encode_err; }

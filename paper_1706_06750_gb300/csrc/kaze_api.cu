@@ -278,12 +278,15 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
             // one FED cycle: n explicit steps from L_{i-1}, alternating between
             // the row-solution scratch plane and L_i so that the last lands in L_i
             KZ_CHECK(conductance(i, Lp, nullptr));
+            // (up to four steps per launch)
             const std::vector<float>& tj = h->fed_tau[i];
-            const int n = (int)tj.size();
+            const std::vector<int> ch = kz::fed_chunks((int)tj.size());
+            const int q = (int)ch.size();
             const float* src = Lp;
-            for (int j = 0; j < n; ++j) {
-                float* dst = ((n - 1 - j) % 2 == 0) ? Li : h->ux;
-                KZ_LAUNCH(h, KK_FED, kz::launch_fed_step(src, h->g, dst, P, w, hh, tj[j], st));
+            for (int c = 0, j = 0; c < q; j += ch[(size_t)c], ++c) {
+                float* dst = ((q - 1 - c) % 2 == 0) ? Li : h->ux;
+                KZ_LAUNCH(h, KK_FED, kz::launch_fed_steps(src, h->g, dst, P, w, hh, tj.data() + j, ch[(size_t)c],
+                                                          h->d_status, st));
                 src = dst;
             }
             continue;
@@ -545,6 +548,10 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
             ce = kz::configure_describe_kernels();
             what = "configure_describe_kernels";
         }
+        if (ce == cudaSuccess) {
+            ce = kz::configure_fed_kernels();
+            what = "configure_fed_kernels";
+        }
         if (ce != cudaSuccess) {
             delete h;
             return create_fail(KAZE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(ce) + " " +
@@ -695,6 +702,17 @@ KAZE_API kaze_status kaze_detect_host(kaze_handle* h, const float* h_img, int w,
     return collect_keypoints(h, h_out, capacity, count);
 }
 
+namespace {
+// waits for the stream and reports a bounded device-side wait that ran out
+kaze_status sync_status(kaze_handle* h)
+{
+    KZ_TRY(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    KZ_TRY(h, cudaStreamSynchronize(h->stream));
+    if (*h->h_status) return fail(h, KAZE_ERR_TIMEOUT, "a bounded device-side wait ran out");
+    return KAZE_OK;
+}
+}  // namespace
+
 KAZE_API kaze_status kaze_op_fed_cycle(kaze_handle* h, const float* d_Lprev, const float* d_g, float* d_scratch,
                                        float* d_Lnext, int pitch, int w, int hh, float dt, int* n_steps)
 {
@@ -709,18 +727,42 @@ KAZE_API kaze_status kaze_op_fed_cycle(kaze_handle* h, const float* d_Lprev, con
     const std::vector<double> tj = kz::fed_ordered_steps((double)dt, (double)h->opt.fed_tau_max);
     const int n = (int)tj.size();
     h->launches = 0;
+    KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
     if (n == 0) {
         KZ_TRY(h, cudaMemcpy2DAsync(d_Lnext, sizeof(float) * pitch, d_Lprev, sizeof(float) * pitch, sizeof(float) * w,
                                     hh, cudaMemcpyDeviceToDevice, h->stream));
     }
+    std::vector<float> tf(tj.begin(), tj.end());
+    const std::vector<int> ch = kz::fed_chunks(n);
+    const int q = (int)ch.size();
     const float* src = d_Lprev;
-    for (int j = 0; j < n; ++j) {
-        float* dst = ((n - 1 - j) % 2 == 0) ? d_Lnext : d_scratch;
-        KZ_LAUNCH(h, KK_FED, kz::launch_fed_step(src, d_g, dst, pitch, w, hh, (float)tj[j], h->stream));
+    for (int c = 0, j = 0; c < q; j += ch[(size_t)c], ++c) {
+        float* dst = ((q - 1 - c) % 2 == 0) ? d_Lnext : d_scratch;
+        KZ_LAUNCH(h, KK_FED,
+                  kz::launch_fed_steps(src, d_g, dst, pitch, w, hh, tf.data() + j, ch[(size_t)c], h->d_status,
+                                       h->stream));
         src = dst;
     }
     if (n_steps) *n_steps = n;
-    return KAZE_OK;
+    return sync_status(h);
+}
+
+KAZE_API kaze_status kaze_op_fed_steps(kaze_handle* h, const float* d_Lprev, const float* d_g, float* d_Lnext,
+                                       int pitch, int w, int hh, const float* h_tau, int k)
+{
+    if (!h || !d_Lprev || !d_g || !d_Lnext || !h_tau) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch < w || pitch % 4) return fail(h, KAZE_ERR_INVALID_ARG, "pitch must be >= w and a multiple of 4");
+    if (((uintptr_t)d_Lprev | (uintptr_t)d_g | (uintptr_t)d_Lnext) & 15)
+        return fail(h, KAZE_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    if (d_Lnext == d_Lprev || d_Lnext == d_g) return fail(h, KAZE_ERR_INVALID_ARG, "output aliases an input");
+    if (k < 1 || k > kz::fed_max_fused()) return fail(h, KAZE_ERR_INVALID_ARG, "k must be 1..4");
+    for (int j = 0; j < k; ++j)
+        if (!std::isfinite(h_tau[j])) return fail(h, KAZE_ERR_INVALID_ARG, "step size not finite");
+    h->launches = 0;
+    KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    KZ_LAUNCH(h, KK_FED, kz::launch_fed_steps(d_Lprev, d_g, d_Lnext, pitch, w, hh, h_tau, k, h->d_status, h->stream));
+    return sync_status(h);
 }
 
 // ---- description (Sec. II-C) -------------------------------------------------

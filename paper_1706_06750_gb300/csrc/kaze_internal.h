@@ -167,6 +167,15 @@ std::vector<double> fed_ordered_steps(double dt, double tau_max);
 // through the border); rows 16-byte aligned, pitch % 4 == 0.
 cudaError_t launch_fed_step(const float* Lin, const float* g, float* Lout, int pitch, int w, int h, float tau,
                             cudaStream_t st);
+// k <= fed_max_fused() consecutive explicit steps (sizes tau[0..k-1]) in one
+// launch, bit-identical to k one-step launches; Lout must not alias Lin or g
+// (a timed-out staging wait sets bit 0 of *status)
+cudaError_t launch_fed_steps(const float* Lin, const float* g, float* Lout, int pitch, int w, int h, const float* tau,
+                             int k, int* status, cudaStream_t st);
+cudaError_t configure_fed_kernels();
+int fed_max_fused();
+// a cycle of n steps split into launches of fed_max_fused() steps and the remainder
+std::vector<int> fed_chunks(int n);
 
 // Orientation and 64-D M-SURF descriptor of n device keypoints (angle
 // written back into d_kps, descriptors to d_desc, n x 64); keypoint k lies on

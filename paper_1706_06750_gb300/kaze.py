@@ -149,6 +149,7 @@ _SIGNATURES = {
     "kaze_build_batch": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _vp, _i,
                               ctypes.POINTER(_i)]),
     "kaze_op_fed_cycle": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _f, ctypes.POINTER(_i)]),
+    "kaze_op_fed_steps": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(_f), _i]),
     "kaze_describe": (_i, [_vp, _vp, _i, _vp, _i]),
     "kaze_describe_device": (_i, [_vp, _vp, _i, _vp, _i]),
     "kaze_op_describe": (_i, [_vp, _vp, _i, _i, _i, _f, _vp, _i, _vp, _i]),
@@ -570,6 +571,17 @@ class Kaze:
                                            float(dt), ctypes.byref(n)), "kaze_op_fed_cycle")
         self._end()
         return int(n.value)
+
+    def op_fed_steps(self, Lprev, g, Lnext, taus):
+        """len(taus) (1..4) explicit steps of Eq. 5 from Lprev into Lnext in
+        one launch, g fixed."""
+        w, h, pitch = _check_image(Lprev)
+        t = (_f * max(len(taus), 1))(*[float(v) for v in taus])
+        self._begin()
+        self._ck(self._L.kaze_op_fed_steps(self._h, _vp(Lprev.data_ptr()), _vp(g.data_ptr()),
+                                           _vp(Lnext.data_ptr()), pitch, w, h, t, len(taus)),
+                 "kaze_op_fed_steps")
+        self._end()
 
     def op_doh(self, L, D, sigma_i, octave):
         w, h, pitch = _check_image(L)

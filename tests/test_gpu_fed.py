@@ -53,6 +53,11 @@ def amplification(t, lam=np.linspace(0.0, 8.0, 2001)):
     return b
 
 
+def launches_for(n):
+    """A cycle of n steps runs as ceil(n / 4) launches of up to four steps."""
+    return -(-n // 4)
+
+
 def oracle_inputs(w, h, seed):
     img = synth.image(w, h, seed).astype(np.float64)
     L0 = oracle.gaussian(img, 1.6).astype(np.float32)
@@ -72,7 +77,7 @@ def test_fed_cycle_matches_oracle(kz, shape, dt):
         x, gd = padded(L0), padded(g)
         scratch, out = padded(np.zeros_like(L0)), padded(np.zeros_like(L0))
         n = k.op_fed_cycle(x, gd, scratch, out, dt)
-        assert k.last_launch_count() == n
+        assert k.last_launch_count() == launches_for(n)
         got = out.cpu().numpy().astype(np.float64)
     ref = oracle.fed_evolve(L0.astype(np.float64), g.astype(np.float64), dt)
     t = oracle.fed_tau(dt)
@@ -111,7 +116,7 @@ def test_pipeline_fed_256(kz):
         lv_g = k.levels().cpu().numpy().astype(np.float64)
         D_g = k.responses().cpu().numpy().astype(np.float64)
     sig, t = oracle.scale_table(2, 4, s0)
-    steps = sum(len(oracle.fed_tau(t[i] - t[i - 1])) for i in range(1, 8))
+    steps = sum(launches_for(len(oracle.fed_tau(t[i] - t[i - 1]))) for i in range(1, 8))
     assert launches == 1 + 1 + 7 + steps + 1 + 1      # presmooth, set k, conductances, steps, doh, extrema
     err = np.max(np.abs(lv_g - lv_r), axis=(1, 2))
     assert np.all(err <= 1e-4), err
@@ -141,3 +146,86 @@ def test_fed_options_validated(kz):
     for bad in (dict(scheme=2), dict(scheme=kz.SCHEME_FED, fed_tau_max=0.3), dict(fed_tau_max=0.0)):
         with pytest.raises(kz.KazeError):
             kz.Kaze(64, 64, **bad)
+
+
+# ---- several explicit steps in one launch --------------------------------------
+
+def cycle_head(dt, k):
+    """The first k step sizes of the FED cycle reaching dt, in its step order."""
+    t = oracle.fed_tau(dt)
+    order, _ = oracle.fed_order(dt)
+    return [float(np.float32(v)) for v in t[order][:k]]
+
+
+@pytest.mark.parametrize("shape", [(3, 3), (5, 121), (97, 131), (33, 250), (40, 483), (1200, 1920)])
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_fused_steps_equal_single_steps(kz, shape, k):
+    """k steps in one launch give, bit for bit, what k one-step launches give
+    (the wavefront sums in the same order); the shapes cover one column of
+    warps, a warp's ragged last lane, several warps and CTAs, and images
+    shorter than a warp's rows."""
+    h, w = shape
+    L0, g = oracle_inputs(w, h, 40 + k + h)
+    taus = cycle_head(67.9, k)
+    with kz.Kaze(w, h) as kk:
+        x, gd = padded(L0), padded(g)
+        fused = padded(np.zeros_like(L0))
+        kk.op_fed_steps(x, gd, fused, taus)
+        assert kk.last_launch_count() == 1
+        a, b = padded(np.zeros_like(L0)), padded(np.zeros_like(L0))
+        src = x
+        for j, t in enumerate(taus):
+            dst = a if j % 2 == 0 else b
+            kk.op_fed_steps(src, gd, dst, [t])
+            src = dst
+        torch.cuda.synchronize()
+        assert torch.equal(fused, src)
+
+
+@pytest.mark.parametrize("shape", [(97, 131), (256, 256)])
+def test_fused_steps_match_oracle(kz, shape):
+    h, w = shape
+    L0, g = oracle_inputs(w, h, 7 + h)
+    taus = cycle_head(30.0, 4)
+    with kz.Kaze(w, h) as kk:
+        x, gd, out = padded(L0), padded(g), padded(np.zeros_like(L0))
+        kk.op_fed_steps(x, gd, out, taus)
+        got = out.cpu().numpy().astype(np.float64)
+    ref = L0.astype(np.float64)
+    for t in taus:
+        ref = oracle.fed_step(ref, g.astype(np.float64), t)
+    tol = 8 * 2.0 ** -24 * amplification(np.array(taus)) * np.abs(L0).max() + 2.0 ** -22
+    assert np.max(np.abs(got - ref)) <= tol
+
+
+def test_fused_steps_ignore_row_padding(kz):
+    """Whatever the padding columns beyond w hold (here NaN), the image's
+    columns do not see it."""
+    h, w = 20, 130
+    L0, g = oracle_inputs(w, h, 3)
+    with kz.Kaze(w, h) as kk:
+        bufs = []
+        for a in (L0, g):
+            buf = torch.full((h, 132), float("nan"), device="cuda")
+            buf[:, :w].copy_(torch.from_numpy(a))
+            bufs.append(buf[:, :w])
+        out = padded(np.zeros_like(L0))
+        ref = padded(np.zeros_like(L0))
+        taus = cycle_head(67.9, 4)
+        kk.op_fed_steps(bufs[0], bufs[1], out, taus)
+        kk.op_fed_steps(padded(L0), padded(g), ref, taus)
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all() and torch.equal(out, ref)
+
+
+def test_fused_steps_arguments_checked(kz):
+    L0, g = oracle_inputs(64, 32, 1)
+    with kz.Kaze(64, 32) as kk:
+        x, gd, out = padded(L0), padded(g), padded(np.zeros_like(L0))
+        for bad in ([], [0.1] * 5):
+            with pytest.raises(kz.KazeError):
+                kk.op_fed_steps(x, gd, out, bad)
+        with pytest.raises(kz.KazeError):
+            kk.op_fed_steps(x, gd, x, [0.1, 0.2])
+        with pytest.raises(kz.KazeError):
+            kk.op_fed_steps(x, gd, out, [0.1, float("inf")])
