@@ -208,6 +208,165 @@ k_gradient(const float* __restrict__ L, float* __restrict__ g, float* __restrict
     }
 }
 
+// The same smoothed Scharr gradient, four columns a lane.  A warp stages
+// 128 columns (X - 4 .. X + 123, float4 loads, reflected into the image) of
+// each needed row in a padded shared-memory row, reads its neighbours
+// there with two 16-byte loads, and writes the 120 columns X .. X + 119
+// (lanes 1..30); lanes 0 and 31 only supply the smoothed values S at X - 1
+// and X + 120.  The radius of G(sigma_d) must be <= 3 so that S(X - 1)
+// only needs the staged columns.  Every value is formed with the
+// arithmetic of k_gradient, operation for operation, so the two kernels
+// (and the batched kernel, which repeats it) agree bit for bit.
+constexpr int C4W = 8;     // warps per CTA
+constexpr int C4K = 8;    // output rows per warp
+constexpr int C4MW = 120;  // output columns per warp
+constexpr int C4PD = 4;    // rows of loads in flight
+
+template <int MODE, int R>
+__global__ void __launch_bounds__(C4W * 32)
+k_gradient4(const float* __restrict__ L, float* __restrict__ g, float* __restrict__ zero, int pitch, int w, int h,
+            const __grid_constant__ GaussTaps taps, const float* __restrict__ d_k, int diffusivity,
+            unsigned int* __restrict__ d_hmax_bits)
+{
+    static_assert(R >= 1 && R <= 3, "S(X - 1) must come from the staged columns");
+    static_assert(MODE == MODE_COND || MODE == MODE_MAX, "conductance or maximum pass");
+    __shared__ __align__(16) float srow[C4W][2][136];  // 4 pad + 128 + 4 pad
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int X = (blockIdx.x * C4W + warp) * C4MW;
+    if (X >= w) return;  // whole warp beyond the image (warps never wait on each other)
+    const int x0 = X - 4 + 4 * lane;
+    const int y0 = blockIdx.y * C4K;
+    if (lane == 0 || lane == 31) {  // the pads only feed unused halo columns; keep them finite
+        const int o = lane == 0 ? 0 : 132;
+        *reinterpret_cast<float4*>(&srow[warp][0][o]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(&srow[warp][1][o]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const bool vec = x0 >= 0 && x0 + 4 <= w;
+    int cx[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cx[q] = reflect_index(x0 + q, w);
+    float wt[R + 1];
+#pragma unroll
+    for (int j = 0; j <= R; ++j) wt[j] = taps.w[R + j];
+    float inv_k2 = 0.f;
+    if (MODE == MODE_COND) {
+        const float kk = *d_k;
+        inv_k2 = 1.f / (kk * kk);
+    }
+    float local_max = 0.f;
+    const bool out_lane = lane >= 1 && lane <= 30 && x0 < w;
+
+    auto load_row = [&](int i) {
+        const int ro = reflect_index(y0 - 1 - R + i, h) * pitch;  // plane offsets fit 32 bits
+        if (vec) return __ldg(reinterpret_cast<const float4*>(L + (unsigned)(ro + x0)));
+        return make_float4(__ldg(L + (unsigned)(ro + cx[0])), __ldg(L + (unsigned)(ro + cx[1])),
+                           __ldg(L + (unsigned)(ro + cx[2])), __ldg(L + (unsigned)(ro + cx[3])));
+    };
+    // H rows y0 - 1 - R .. y0 + C4K + R; S rows y0 - 1 .. y0 + C4K
+    constexpr int NI = C4K + 2 + 2 * R;
+    float4 pre[C4PD + 1];
+#pragma unroll
+    for (int i = 0; i < C4PD && i < NI; ++i) pre[i] = load_row(i);
+    float hw[2 * R + 1][4];  // last 2R + 1 horizontally filtered rows
+    float dm[4], d0[4], em[4], e0[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dm[q] = d0[q] = em[q] = e0[q] = 0.f;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        if (i + C4PD < NI) pre[(i + C4PD) % (C4PD + 1)] = load_row(i + C4PD);
+        float* sr_ = srow[warp][i & 1];
+        const float4 c = pre[i % (C4PD + 1)];
+        *reinterpret_cast<float4*>(sr_ + 4 + 4 * lane) = c;
+        __syncwarp();
+        const float4 a = *reinterpret_cast<const float4*>(sr_ + 4 * lane);
+        const float4 b = *reinterpret_cast<const float4*>(sr_ + 8 + 4 * lane);
+        const float v[12] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, b.x, b.y, b.z, b.w};  // columns x0 - 4 ..
+#pragma unroll
+        for (int j = 0; j < 2 * R; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) hw[j][q] = hw[j + 1][q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float hv = wt[0] * v[4 + q];
+#pragma unroll
+            for (int j = 1; j <= R; ++j) hv = fmaf(wt[j], v[4 + q - j] + v[4 + q + j], hv);
+            hw[2 * R][q] = hv;
+        }
+        if (i < 2 * R) continue;
+        // S at row y0 - 1 + (i - 2R)
+        float sv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            sv[q] = wt[0] * hw[R][q];
+#pragma unroll
+            for (int j = 1; j <= R; ++j) sv[q] = fmaf(wt[j], hw[R - j][q] + hw[R + j][q], sv[q]);
+        }
+        const float s_l = __shfl_up_sync(0xffffffffu, sv[3], 1);
+        const float s_r = __shfl_down_sync(0xffffffffu, sv[0], 1);
+        float dp[4], ep[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float sl = q == 0 ? s_l : sv[q - 1];
+            const float sr = q == 3 ? s_r : sv[q + 1];
+            dp[q] = sr - sl;
+            ep[q] = fmaf(10.f, sv[q], 3.f * (sl + sr));
+        }
+        const int si = i - 2 * R;
+        if (si >= 2) {
+            const int y = y0 + si - 2;  // output row: S rows y - 1, y, y + 1
+            float m2[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float lx = fmaf(10.f, d0[q], 3.f * (dm[q] + dp[q])) * (1.f / 32.f);
+                const float ly = (ep[q] - em[q]) * (1.f / 32.f);
+                m2[q] = fmaf(ly, ly, lx * lx);
+            }
+            if (out_lane && y < h) {
+                const unsigned o = (unsigned)(y * pitch + x0);
+                float4 r;
+                if (MODE == MODE_COND) {
+                    float* rr = &r.x;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        rr[q] = diffusivity == KAZE_G1 ? expf(-(m2[q] * inv_k2))
+                                                       : __fdividef(1.f, fmaf(m2[q], inv_k2, 1.f));
+                } else {
+                    r = make_float4(m2[0], m2[1], m2[2], m2[3]);
+                    if (y >= 1 && y <= h - 2) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (x0 + q >= 1 && x0 + q <= w - 2) local_max = fmaxf(local_max, sqrtf(m2[q]));
+                    }
+                }
+                if (MODE == MODE_COND || g) {
+                    if (x0 + 4 <= w) {
+                        *reinterpret_cast<float4*>(g + o) = r;
+                        if (MODE == MODE_COND && zero) *reinterpret_cast<float4*>(zero + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else {
+                        const float* rr = &r.x;
+                        for (int q = 0; q < 4 && x0 + q < w; ++q) {
+                            g[o + q] = rr[q];
+                            if (MODE == MODE_COND && zero) zero[o + q] = 0.f;
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            dm[q] = d0[q];
+            d0[q] = dp[q];
+            em[q] = e0[q];
+            e0[q] = ep[q];
+        }
+    }
+    if (MODE == MODE_MAX) {
+        for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+        // non-negative floats order like their bit patterns
+        if (lane == 0 && local_max > 0.f) atomicMax(d_hmax_bits, __float_as_uint(local_max));
+    }
+}
+
 // Percentile pick on one warp: lane l owns a contiguous slice of bins, the
 // slice sums are prefix-summed with shuffles, and the lane whose slice
 // crosses pct * n walks its bins.  k = hmax * (b + 1) / nbins; 0.03 when no
@@ -344,11 +503,32 @@ cudaError_t launch_gradient_r(const float* L, float* g, float* zero, int pitch, 
     return cudaGetLastError();
 }
 
+template <int MODE, int R>
+cudaError_t launch_gradient4_r(const float* L, float* g, float* zero, int pitch, int w, int h, const GaussTaps& taps,
+                               const float* d_k, int diffusivity, unsigned int* hmax_bits, cudaStream_t st)
+{
+    dim3 grid((w + C4W * C4MW - 1) / (C4W * C4MW), (h + C4K - 1) / C4K);
+    k_gradient4<MODE, R><<<grid, C4W * 32, 0, st>>>(L, g, zero, pitch, w, h, taps, d_k, diffusivity, hmax_bits);
+    return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch_gradient(const float* L, float* g, float* zero, int pitch, int w, int h, const GaussTaps& taps,
                             const float* d_k, int diffusivity, unsigned int* hmax_bits, unsigned int* hist,
                             int nbins, cudaStream_t st)
 {
+    // four columns a lane where the radius allows it and the planes take
+    // 16-byte accesses
+    const bool aligned = (pitch & 3) == 0 && (((uintptr_t)L | (uintptr_t)g | (uintptr_t)zero) & 15) == 0;
+    if constexpr (MODE != MODE_HIST) {
+        if (aligned && taps.r >= 1 && taps.r <= 3) {
+            switch (taps.r) {
+            case 1: return launch_gradient4_r<MODE, 1>(L, g, zero, pitch, w, h, taps, d_k, diffusivity, hmax_bits, st);
+            case 2: return launch_gradient4_r<MODE, 2>(L, g, zero, pitch, w, h, taps, d_k, diffusivity, hmax_bits, st);
+            default: return launch_gradient4_r<MODE, 3>(L, g, zero, pitch, w, h, taps, d_k, diffusivity, hmax_bits, st);
+            }
+        }
+    }
     switch (taps.r) {
 #define KZ_GRAD_CASE(RR) \
     case RR: return launch_gradient_r<MODE, RR>(L, g, zero, pitch, w, h, taps, d_k, diffusivity, hmax_bits, hist, nbins, st);

@@ -124,6 +124,43 @@ def test_conductance_step(kz, shape, diff):
     assert np.max(np.abs(host(g) - ref)) < 2e-5
 
 
+def misaligned(a, pitch):
+    """A [h, w] view with row pitch `pitch` whose first element is 4 bytes past
+    a 16-byte boundary (the library then takes its one-column-a-lane
+    gradient kernel instead of the four-column one)."""
+    h, w = a.shape
+    base = torch.zeros(h * pitch + 8, device="cuda")
+    v = base[1:1 + h * pitch].view(h, pitch)[:, :w]
+    v.copy_(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)))
+    assert v.data_ptr() % 16 == 4
+    return v
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (131, 257), (3, 5), (40, 483), (1200, 1920)])
+@pytest.mark.parametrize("diff", [2, 1])
+def test_conductance_kernels_agree_bitwise(kz, shape, diff):
+    """The four-column gradient kernel (aligned planes) and the one-column
+    kernel (any alignment) form the conductance with the same operations in
+    the same order: equal bit for bit, also at ragged widths and borders."""
+    rng = np.random.default_rng(12)
+    h, w = shape
+    L = random_smooth(rng, h, w).astype(np.float32)
+    pitch = (w + 3) // 4 * 4
+    with kz.Kaze(w, h, diffusivity=diff) as k:
+        buf = torch.zeros((h, pitch), device="cuda")
+        a = buf[:, :w]
+        a.copy_(torch.from_numpy(L))
+        ga = torch.zeros((h, pitch), device="cuda")[:, :w]
+        k.op_conductance(a, ga, 0.02)
+        b = misaligned(L, pitch + 4)
+        gb = misaligned(np.zeros_like(L), pitch + 4)
+        k.op_conductance(b, gb, 0.02)
+        torch.cuda.synchronize()
+        assert torch.equal(ga, gb)
+        # the maximum pass of the contrast factor, both ways
+        assert k.op_contrast(a)[:2] == k.op_contrast(b)[:2]
+
+
 @pytest.mark.parametrize("shape", [(256, 256), (131, 257), (3, 3), (4, 61), (61, 4),
                                    (40, 2100), (2100, 40), (1200, 1920)])
 @pytest.mark.parametrize("tau", [0.53, 67.9])
