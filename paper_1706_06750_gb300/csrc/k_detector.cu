@@ -43,8 +43,7 @@ k_doh(const float* __restrict__ L, float* __restrict__ D, int pitch, long long p
     const int x = blockIdx.x * WTX + threadIdx.x;
     const int k0 = seg * WK;
     if (py >= s || x >= w || py + s * k0 >= h) return;
-    const double dd = 1024.0 * s * s;
-    const float scale = (float)((double)tab.norm[level] / (dd * dd));  // as the batched path computes it
+    const float scale = tab.doh_scale[level];
     L += (size_t)level * plane_stride;
     D += (size_t)level * plane_stride;
     int cx[5];
@@ -190,8 +189,16 @@ cudaError_t launch_doh(const float* L, float* D, int pitch, long long plane_stri
         gy = s * nseg > gy ? s * nseg : gy;
     }
     if (gy > 65535) return cudaErrorInvalidValue;
+    // the determinant's scale in double on the host (the batched path forms
+    // it the same way): a double division per thread would keep the GPU's
+    // slow FP64 pipe busy for a third of the launch
+    LevelTable t = tab;
+    for (int i = l0; i < l0 + nl; ++i) {
+        const double dd = 1024.0 * t.step[i] * t.step[i];
+        t.doh_scale[i] = (float)((double)t.norm[i] / (dd * dd));
+    }
     dim3 grid((w + WTX - 1) / WTX, gy, nl);
-    k_doh<<<grid, WTX, 0, st>>>(L, D, pitch, plane_stride, w, h, l0, tab);
+    k_doh<<<grid, WTX, 0, st>>>(L, D, pitch, plane_stride, w, h, l0, t);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ struct LevelTable {
     float sigma[kMaxLevels];     // sigma_i
     int sublevels;               // S (octave = i / S, sublevel = i % S)
     int xr[kMaxLevels];          // cross-level radius of the maximum test (1: 3x3x3)
+    float doh_scale[kMaxLevels]; // norm / (1024 s^2)^2, filled by launch_doh
 };
 
 // Per-level constants of keypoint description (Sec. II-C), passed by value.
