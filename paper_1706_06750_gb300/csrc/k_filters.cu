@@ -10,6 +10,8 @@
 // columns.  The gradient kernels walk down columns instead (see k_gradient):
 // each thread keeps its vertical filter window in registers and trades
 // neighbouring columns by warp shuffles, with no shared-memory staging.
+#include <algorithm>
+
 #include "kaze_internal.h"
 
 namespace kz {
@@ -427,20 +429,32 @@ k_hist_m2(const float* __restrict__ m2p, int pitch, int w, int h, const unsigned
     for (int i = threadIdx.x; i < nbins; i += blockDim.x) hist_s[i] = 0u;
     __syncthreads();
     const float hmax_scale = (float)nbins / __uint_as_float(*d_hmax_bits);
-    const int y = blockIdx.y;
     const int x4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    if (y >= 1 && y <= h - 2 && x4 < w) {
-        const float4 v4 = __ldg(reinterpret_cast<const float4*>(m2p + (unsigned)(y * pitch + x4)));
-        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+    // rows blockIdx.y, + gridDim.y, ...: a few CTAs an SM each flush their
+    // shared histogram once, HB rows of loads in flight at a time
+    constexpr int HB = 4;
+    for (int y0 = blockIdx.y; y0 < h; y0 += HB * gridDim.y) {
+        float4 v4[HB];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int x = x4 + q;
-            if (x < 1 || x > w - 2) continue;
-            const float m = sqrtf(v[q]);
-            if (m > 0.f) {
-                int b = (int)floorf(m * hmax_scale);
-                b = min(b, nbins - 1);
-                atomicAdd(&hist_s[b], 1u);
+        for (int k = 0; k < HB; ++k) {
+            const int y = y0 + k * gridDim.y;
+            v4[k] = (y >= 1 && y <= h - 2 && x4 < w)
+                        ? __ldg(reinterpret_cast<const float4*>(m2p + (unsigned)(y * pitch + x4)))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < HB; ++k) {
+            const float v[4] = {v4[k].x, v4[k].y, v4[k].z, v4[k].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int x = x4 + q;
+                if (x < 1 || x > w - 2) continue;
+                const float m = sqrtf(v[q]);  // rows outside 1..h-2 read as 0: not binned
+                if (m > 0.f) {
+                    int b = (int)floorf(m * hmax_scale);
+                    b = min(b, nbins - 1);
+                    atomicAdd(&hist_s[b], 1u);
+                }
             }
         }
     }
@@ -586,7 +600,9 @@ cudaError_t launch_hist_m2(const float* m2, int pitch, int w, int h, const unsig
 {
     if ((pitch & 3) || ((uintptr_t)m2 & 15)) return cudaErrorInvalidValue;
     const int tx = (w + 3) / 4;
-    dim3 grid((tx + 255) / 256, h);
+    const int gx = (tx + 255) / 256;
+    const int gy = std::max(1, std::min(h, 608 / gx));  // about four CTAs an SM
+    dim3 grid(gx, gy);
     k_hist_m2<<<grid, 256, (size_t)nbins * sizeof(unsigned int), st>>>(m2, pitch, w, h, d_hmax_bits, d_hist, nbins,
                                                                         pct, d_k);
     return cudaGetLastError();
