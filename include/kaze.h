@@ -167,6 +167,18 @@ kaze_status kaze_detect(kaze_handle* h, const float* d_img, int w, int h_, int p
 kaze_status kaze_detect_host(kaze_handle* h, const float* h_img, int w, int h_, int pitch_elems,
                              kaze_keypoint* h_out, int capacity, int* count);
 
+/* kaze_detect_host for a stream of host images: also starts copying h_next
+ * (the next image: same w, h_ and pitch; NULL for none) to the device on a
+ * second stream while h_img is detected, into the other of the handle's
+ * two input planes.  A following kaze_detect_host or kaze_detect_host_next
+ * whose h_img is that h_next (same size and pitch) then detects the copy
+ * already on the device instead of copying again.  h_next must stay valid
+ * and unchanged until that call, and be page-locked for the copy to
+ * overlap.  Keypoints, count and errors as kaze_detect_host; synchronises
+ * the handle's stream (the copy of h_next may still be in flight). */
+kaze_status kaze_detect_host_next(kaze_handle* h, const float* h_img, const float* h_next, int w, int h_,
+                                  int pitch_elems, kaze_keypoint* h_out, int capacity, int* count);
+
 /* ---- description (Sec. II-C) --------------------------------------------- *
  * Dominant orientation and 64-D M-SURF descriptor of keypoints on the levels
  * of the last kaze_build_scale_space (any level of the stack, all in one

@@ -49,6 +49,7 @@ struct kaze_handle {
     float* g = nullptr;            // conductance scratch
     float* ux = nullptr;           // row-solution scratch
     float* staging = nullptr;      // device copy of a host input image
+    float* staging2 = nullptr;     // a second one: the next host image arrives here while one is detected
     float* d_k = nullptr;          // contrast factor
     unsigned int* d_hmax = nullptr;
     unsigned int* d_hist = nullptr;
@@ -81,15 +82,25 @@ struct kaze_handle {
     std::vector<int> batch_w, batch_h;
     float sg_s[kz::kMaxLevels];  // BF16 value of log(1 + tau_i) / 5 per level
 
-    // recorded detection graph
-    cudaGraphExec_t gexec = nullptr;
-    const float* g_img = nullptr;
-    int g_w = 0, g_h = 0, g_pitch = 0;
+    // recorded detection graphs, one per (input plane, size): two slots, so
+    // that the two staging planes of a stream of host images both keep theirs
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        const float* img = nullptr;
+        int w = 0, h = 0, pitch = 0, launches = 0;
+    } gslot[2];
+    int g_last = 0;  // slot used last
+
+    // the next host image, copied on `copy` while the current one is detected
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_copied = nullptr;
+    const float* pre_src = nullptr;
+    int pre_slot = -1, pre_w = 0, pre_h = 0, pre_pitch = 0;
+    bool pre_issued = false;  // a copy was issued on `copy` (the main stream waits for it before reusing a plane)
 
     // launch accounting: kernels enqueued by the current pipeline call, and
     // optional event pairs around each launch (kaze_profile)
     int launches = 0;
-    int graph_launches = 0;
     bool profiling = false;
     struct ProfEntry {
         int kind, kernels;
@@ -362,9 +373,10 @@ kaze_status collect_keypoints(kaze_handle* h, kaze_keypoint* out, int capacity, 
 
 void drop_graph(kaze_handle* h)
 {
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-    h->g_img = nullptr;
+    for (auto& g : h->gslot) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = kaze_handle::GraphSlot();
+    }
 }
 
 // Records build + response + extrema once per (input pointer, size) and
@@ -378,8 +390,16 @@ kaze_status run_detect_graph(kaze_handle* h, const float* d_img, int w, int hh, 
         KZ_CHECK(enqueue_response(h));
         return enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab);
     }
-    if (!(h->gexec && h->g_img == d_img && h->g_w == w && h->g_h == hh && h->g_pitch == pitch)) {
-        drop_graph(h);
+    int slot = -1;
+    for (int i = 0; i < 2; ++i) {
+        const kaze_handle::GraphSlot& g = h->gslot[i];
+        if (g.exec && g.img == d_img && g.w == w && g.h == hh && g.pitch == pitch) slot = i;
+    }
+    if (slot < 0) {
+        slot = 1 - h->g_last;  // replace the slot used less recently
+        kaze_handle::GraphSlot& g = h->gslot[slot];
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = kaze_handle::GraphSlot();
         cudaGraph_t graph = nullptr;
         h->launches = 0;
         KZ_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -392,21 +412,22 @@ kaze_status run_detect_graph(kaze_handle* h, const float* d_img, int w, int hh, 
             return s;
         }
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&h->gexec, graph, 0);
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
-            h->gexec = nullptr;
+            g.exec = nullptr;
             return cuda_fail(h, e, "cudaGraphInstantiate");
         }
-        h->graph_launches = h->launches;
-        h->g_img = d_img;
-        h->g_w = w;
-        h->g_h = hh;
-        h->g_pitch = pitch;
+        g.launches = h->launches;
+        g.img = d_img;
+        g.w = w;
+        g.h = hh;
+        g.pitch = pitch;
     }
+    h->g_last = slot;
     set_geometry(h, w, hh);
-    KZ_TRY(h, cudaGraphLaunch(h->gexec, h->stream));
-    h->launches = h->graph_launches;
+    KZ_TRY(h, cudaGraphLaunch(h->gslot[slot].exec, h->stream));
+    h->launches = h->gslot[slot].launches;
     h->built = true;
     h->responded = true;
     return KAZE_OK;
@@ -567,6 +588,7 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     const size_t off_g = bytes;      bytes += al(sizeof(float) * pm);
     const size_t off_ux = bytes;     bytes += al(sizeof(float) * pm);
     const size_t off_stage = bytes;  bytes += al(sizeof(float) * pm);
+    const size_t off_stage2 = bytes; bytes += al(sizeof(float) * pm);
     const size_t off_k = bytes;      bytes += al(sizeof(float));
     const size_t off_hmax = bytes;   bytes += al(sizeof(unsigned int));
     const size_t off_hist = bytes;   bytes += al(sizeof(unsigned int) * (o.nbins + 1));  // + a block counter
@@ -587,6 +609,7 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     h->g = (float*)(a + off_g);
     h->ux = (float*)(a + off_ux);
     h->staging = (float*)(a + off_stage);
+    h->staging2 = (float*)(a + off_stage2);
     h->d_k = (float*)(a + off_k);
     h->d_hmax = (unsigned int*)(a + off_hmax);
     h->d_hist = (unsigned int*)(a + off_hist);
@@ -605,8 +628,10 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     h->h_status = (int*)(h->h_count + 1);
     *h->h_status = 0;
     if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+        (e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming)) != cudaSuccess) {
         kaze_destroy(h);
         return create_fail(KAZE_ERR_CUDA, std::string("stream / event creation: ") + cudaGetErrorName(e));
     }
@@ -688,18 +713,61 @@ KAZE_API kaze_status kaze_detect(kaze_handle* h, const float* d_img, int w, int 
     return collect_keypoints(h, h_out, capacity, count);
 }
 
-KAZE_API kaze_status kaze_detect_host(kaze_handle* h, const float* h_img, int w, int hh, int pitch_elems,
-                                      kaze_keypoint* h_out, int capacity, int* count)
+namespace {
+// Detection of a host image through the staging planes: the image is the
+// one copied ahead by the previous call (same pointer, size and pitch), or
+// is copied now; with h_next, the next image is copied into the other plane
+// on the copy stream while this one is detected.
+kaze_status detect_host_impl(kaze_handle* h, const float* h_img, const float* h_next, int w, int hh,
+                             int pitch_elems, kaze_keypoint* h_out, int capacity, int* count)
 {
     if (!h || !h_img || capacity < 0 || (capacity > 0 && !h_out))
         return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
     KZ_CHECK(check_image(h, w, hh));
     if (pitch_elems < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
     const int sp = pitch_for(w);
-    KZ_TRY(h, cudaMemcpy2DAsync(h->staging, sizeof(float) * sp, h_img, sizeof(float) * pitch_elems,
-                                sizeof(float) * w, hh, cudaMemcpyHostToDevice, h->stream));
-    KZ_CHECK(run_detect_graph(h, h->staging, w, hh, sp));
+    float* planes[2] = {h->staging, h->staging2};
+    // the main stream never touches a plane before a copy issued into it has landed
+    if (h->pre_issued) KZ_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_copied, 0));
+    int slot;
+    if (h->pre_slot >= 0 && h->pre_src == h_img && h->pre_w == w && h->pre_h == hh && h->pre_pitch == pitch_elems) {
+        slot = h->pre_slot;
+    } else {
+        slot = h->pre_slot >= 0 ? 1 - h->pre_slot : 0;
+        KZ_TRY(h, cudaMemcpy2DAsync(planes[slot], sizeof(float) * sp, h_img, sizeof(float) * pitch_elems,
+                                    sizeof(float) * w, hh, cudaMemcpyHostToDevice, h->stream));
+    }
+    h->pre_slot = -1;
+    h->pre_src = nullptr;
+    KZ_CHECK(run_detect_graph(h, planes[slot], w, hh, sp));
+    if (h_next) {
+        // the other plane was last read by the previous detection, which the
+        // previous call waited for (collect_keypoints synchronises)
+        const int other = 1 - slot;
+        KZ_TRY(h, cudaMemcpy2DAsync(planes[other], sizeof(float) * sp, h_next, sizeof(float) * pitch_elems,
+                                    sizeof(float) * w, hh, cudaMemcpyHostToDevice, h->copy));
+        KZ_TRY(h, cudaEventRecord(h->ev_copied, h->copy));
+        h->pre_issued = true;
+        h->pre_src = h_next;
+        h->pre_slot = other;
+        h->pre_w = w;
+        h->pre_h = hh;
+        h->pre_pitch = pitch_elems;
+    }
     return collect_keypoints(h, h_out, capacity, count);
+}
+}  // namespace
+
+KAZE_API kaze_status kaze_detect_host(kaze_handle* h, const float* h_img, int w, int hh, int pitch_elems,
+                                      kaze_keypoint* h_out, int capacity, int* count)
+{
+    return detect_host_impl(h, h_img, nullptr, w, hh, pitch_elems, h_out, capacity, count);
+}
+
+KAZE_API kaze_status kaze_detect_host_next(kaze_handle* h, const float* h_img, const float* h_next, int w, int hh,
+                                           int pitch_elems, kaze_keypoint* h_out, int capacity, int* count)
+{
+    return detect_host_impl(h, h_img, h_next, w, hh, pitch_elems, h_out, capacity, count);
 }
 
 namespace {
@@ -1110,8 +1178,10 @@ KAZE_API void kaze_destroy(kaze_handle* h)
     if (h->h_count) cudaFreeHost(h->h_count);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_copied) cudaEventDestroy(h->ev_copied);
     if (h->own_surrogate) kaze_surrogate_destroy(h->own_surrogate);
     if (h->batch) kaze_batch_destroy(h->batch);
     if (h->side) cudaStreamDestroy(h->side);
+    if (h->copy) cudaStreamDestroy(h->copy);
     delete h;
 }

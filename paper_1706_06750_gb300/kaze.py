@@ -100,6 +100,7 @@ _SIGNATURES = {
     "kaze_find_extrema": (_i, [_vp, ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
     "kaze_detect": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
     "kaze_detect_host": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
+    "kaze_detect_host_next": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
     "kaze_op_gaussian": (_i, [_vp, _vp, _i, _vp, _i, _i, _i, _f]),
     "kaze_op_contrast": (_i, [_vp, _vp, _i, _i, _i, ctypes.POINTER(_f), ctypes.POINTER(_f),
                               ctypes.POINTER(ctypes.c_uint)]),
@@ -390,22 +391,38 @@ class Kaze:
         self.last_count = n.value
         return _sorted_keypoints(buf, min(n.value, cap))
 
-    def detect_host(self, img, capacity=None):
-        """kaze_detect on a host image (numpy array or CPU tensor, float32)."""
+    @staticmethod
+    def _host_image(img):
+        """(pointer, h, w, pitch, keep-alive) of a 2-D float32 host image."""
         import torch
         if isinstance(img, torch.Tensor):
             if img.is_cuda or img.dtype != torch.float32 or img.dim() != 2 or img.stride(1) != 1:
                 raise KazeError(ERR_INVALID_ARG, "expected a 2-D float32 CPU tensor")
-            ptr, h, w, pitch = img.data_ptr(), img.shape[0], img.shape[1], img.stride(0)
-        else:
-            img = np.ascontiguousarray(img, dtype=np.float32)
-            ptr, (h, w), pitch = img.ctypes.data, img.shape, img.shape[1]
+            return img.data_ptr(), img.shape[0], img.shape[1], img.stride(0), img
+        img = np.ascontiguousarray(img, dtype=np.float32)
+        return img.ctypes.data, img.shape[0], img.shape[1], img.shape[1], img
+
+    def detect_host(self, img, capacity=None, next=None):
+        """kaze_detect on a host image (numpy array or CPU tensor, float32).
+        With `next` (the following image: same size and row stride, kept
+        alive and unchanged until it is detected, ideally pinned), its copy to
+        the device starts while `img` is detected (kaze_detect_host_next)."""
+        ptr, h, w, pitch, keep = self._host_image(img)
         cap = self.options.max_keypoints if capacity is None else int(capacity)
         buf = self._kp_buf if cap <= len(self._kp_buf) else (Keypoint * cap)()
         n = _i()
         self._begin()
-        st = self._ck(self._L.kaze_detect_host(self._h, _vp(ptr), w, h, pitch, buf, cap,
-                                               ctypes.byref(n)), "kaze_detect_host")
+        if next is None:
+            st = self._ck(self._L.kaze_detect_host(self._h, _vp(ptr), w, h, pitch, buf, cap, ctypes.byref(n)),
+                          "kaze_detect_host")
+        else:
+            nptr, nh, nw, npitch, nkeep = self._host_image(next)
+            if (nh, nw, npitch) != (h, w, pitch):
+                raise KazeError(ERR_INVALID_ARG, "the next image must have the same size and row stride")
+            self._next_keep = nkeep
+            st = self._ck(self._L.kaze_detect_host_next(self._h, _vp(ptr), _vp(nptr), w, h, pitch, buf, cap,
+                                                        ctypes.byref(n)), "kaze_detect_host_next")
+        del keep
         self._end()
         self._w, self._hh = w, h
         self.last_status = st

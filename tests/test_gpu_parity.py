@@ -322,6 +322,34 @@ def test_detect_graph_equals_eager_and_host_path(kz):
         assert np.array_equal(eager, other)
 
 
+def test_detect_host_next_streams_images(kz):
+    """A stream of host images with the next one copied ahead (two input
+    planes, two recorded graphs): every result equals the image detected on
+    its own, also when a copied-ahead image is skipped, a device detection
+    comes in between, or the size of the next image differs (rejected)."""
+    imgs = [synth.image(320, 240, 50 + j) for j in range(4)]
+    pinned = [torch.from_numpy(a).pin_memory() for a in imgs]
+    with kz.Kaze(320, 240, octaves=2, sublevels=4) as k:
+        alone = [k.detect_host(a) for a in imgs]
+        assert all(len(r) > 0 for r in alone)
+        got = [k.detect_host(pinned[0], next=pinned[1]),
+               k.detect_host(pinned[1], next=pinned[2]),
+               k.detect_host(pinned[2], next=pinned[3]),
+               k.detect_host(pinned[3])]
+        for a, b in zip(alone, got):
+            assert np.array_equal(a, b)
+        # copy ahead of 1, then detect 3 instead, then a device image, then 1
+        r1 = k.detect_host(pinned[0], next=pinned[1])
+        r3 = k.detect_host(pinned[3], next=pinned[2])
+        rd = k.detect(dev(imgs[2]))
+        r2 = k.detect_host(pinned[2], next=pinned[1])
+        r4 = k.detect_host(pinned[1])
+        for a, b in ((alone[0], r1), (alone[3], r3), (alone[2], rd), (alone[2], r2), (alone[1], r4)):
+            assert np.array_equal(a, b)
+        with pytest.raises(kz.KazeError):
+            k.detect_host(pinned[0], next=torch.zeros((240, 300)).pin_memory())
+
+
 def test_capacity_overflow_reports_true_count(kz):
     img = synth.workload_image("256x256")
     with kz.Kaze(256, 256, octaves=2, sublevels=4) as k:
