@@ -1173,6 +1173,7 @@ KAZE_API const char* kaze_last_error(const kaze_handle* h)
 KAZE_API void kaze_destroy(kaze_handle* h)
 {
     if (!h) return;
+    if (h->copy) cudaStreamSynchronize(h->copy);  // a copy of the next host image may still be landing
     drop_graph(h);
     if (h->arena) cudaFree(h->arena);
     if (h->h_count) cudaFreeHost(h->h_count);
