@@ -356,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
     for i in range(args.warmup):
         k.detect(x)
         k.detect_host(pinned)
-        k.detect_host(stream_bufs[i % 2], next=stream_bufs[(i + 1) % 2])
+        k.detect_host(stream_bufs[i % 2], next_image=stream_bufs[(i + 1) % 2])
     n_kp = len(k.detect(x))
     launches = k.last_launch_count()
 
@@ -381,13 +381,13 @@ def run_ours(args, rank, world, local_rank):
     t_single_ms = timed(lambda: k.detect_host(pinned))
     barrier()
     # the stream: the first timed image is copied ahead by this call
-    k.detect_host(stream_bufs[1], next=stream_bufs[0])
+    k.detect_host(stream_bufs[1], next_image=stream_bufs[0])
     step = [0]
 
     def stream_step():
         i = step[0]
         step[0] += 1
-        k.detect_host(stream_bufs[i % 2], next=stream_bufs[(i + 1) % 2])
+        k.detect_host(stream_bufs[i % 2], next_image=stream_bufs[(i + 1) % 2])
 
     t_e2e_ms = timed(stream_step)
     barrier()

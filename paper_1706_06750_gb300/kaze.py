@@ -402,24 +402,25 @@ class Kaze:
         img = np.ascontiguousarray(img, dtype=np.float32)
         return img.ctypes.data, img.shape[0], img.shape[1], img.shape[1], img
 
-    def detect_host(self, img, capacity=None, next=None):
+    def detect_host(self, img, capacity=None, next_image=None):
         """kaze_detect on a host image (numpy array or CPU tensor, float32).
-        With `next` (the following image: same size and row stride, kept
+        With `next_image` (the following image: same size and row stride, kept
         alive and unchanged until it is detected, ideally pinned), its copy to
         the device starts while `img` is detected (kaze_detect_host_next)."""
         ptr, h, w, pitch, keep = self._host_image(img)
+        if next_image is not None:
+            nptr, nh, nw, npitch, nkeep = self._host_image(next_image)
+            if (nh, nw, npitch) != (h, w, pitch):
+                raise KazeError(ERR_INVALID_ARG, "the next image must have the same size and row stride")
         cap = self.options.max_keypoints if capacity is None else int(capacity)
         buf = self._kp_buf if cap <= len(self._kp_buf) else (Keypoint * cap)()
         n = _i()
         self._begin()
-        if next is None:
+        if next_image is None:
             st = self._ck(self._L.kaze_detect_host(self._h, _vp(ptr), w, h, pitch, buf, cap, ctypes.byref(n)),
                           "kaze_detect_host")
         else:
-            nptr, nh, nw, npitch, nkeep = self._host_image(next)
-            if (nh, nw, npitch) != (h, w, pitch):
-                raise KazeError(ERR_INVALID_ARG, "the next image must have the same size and row stride")
-            self._next_keep = nkeep
+            self._next_keep = nkeep  # the copy reads it after this call returns
             st = self._ck(self._L.kaze_detect_host_next(self._h, _vp(ptr), _vp(nptr), w, h, pitch, buf, cap,
                                                         ctypes.byref(n)), "kaze_detect_host_next")
         del keep

@@ -332,22 +332,22 @@ def test_detect_host_next_streams_images(kz):
     with kz.Kaze(320, 240, octaves=2, sublevels=4) as k:
         alone = [k.detect_host(a) for a in imgs]
         assert all(len(r) > 0 for r in alone)
-        got = [k.detect_host(pinned[0], next=pinned[1]),
-               k.detect_host(pinned[1], next=pinned[2]),
-               k.detect_host(pinned[2], next=pinned[3]),
+        got = [k.detect_host(pinned[0], next_image=pinned[1]),
+               k.detect_host(pinned[1], next_image=pinned[2]),
+               k.detect_host(pinned[2], next_image=pinned[3]),
                k.detect_host(pinned[3])]
         for a, b in zip(alone, got):
             assert np.array_equal(a, b)
         # copy ahead of 1, then detect 3 instead, then a device image, then 1
-        r1 = k.detect_host(pinned[0], next=pinned[1])
-        r3 = k.detect_host(pinned[3], next=pinned[2])
+        r1 = k.detect_host(pinned[0], next_image=pinned[1])
+        r3 = k.detect_host(pinned[3], next_image=pinned[2])
         rd = k.detect(dev(imgs[2]))
-        r2 = k.detect_host(pinned[2], next=pinned[1])
+        r2 = k.detect_host(pinned[2], next_image=pinned[1])
         r4 = k.detect_host(pinned[1])
         for a, b in ((alone[0], r1), (alone[3], r3), (alone[2], rd), (alone[2], r2), (alone[1], r4)):
             assert np.array_equal(a, b)
         with pytest.raises(kz.KazeError):
-            k.detect_host(pinned[0], next=torch.zeros((240, 300)).pin_memory())
+            k.detect_host(pinned[0], next_image=torch.zeros((240, 300)).pin_memory())
 
 
 def test_capacity_overflow_reports_true_count(kz):
