@@ -1,15 +1,18 @@
 // k_filters.cu -- stencil kernels of the nonlinear scale space (Sec. III-1):
 //   * Gaussian presmoothing of the input image,
 //   * the fused "smooth -> Scharr -> conductance" kernel (Eq. 2-3),
-//   * the two gradient-statistics passes and the percentile pick that give
-//     the contrast factor k from the gradient histogram.
+//   * the gradient-statistics passes (maximum, histogram of the kept |grad|^2
+//     plane) and the percentile pick that give the contrast factor k.
 //
 // Presmoothing: a CTA of 32x8 threads owns a 32x32 output tile, stages its
 // input tile plus halo in shared memory with half-sample symmetric borders
 // (index reflection on load) and runs the separable Gaussian rows-then-
-// columns.  The gradient kernels walk down columns instead (see k_gradient):
-// each thread keeps its vertical filter window in registers and trades
-// neighbouring columns by warp shuffles, with no shared-memory staging.
+// columns.  The gradient kernels walk down columns instead: a warp stages
+// each needed row in a small shared-memory row for the horizontal taps,
+// keeps the vertical filter window in registers and trades neighbouring
+// smoothed values by warp shuffles -- one column a lane (k_gradient) or four
+// (k_gradient4, used wherever the planes allow 16-byte access), with the
+// same arithmetic.
 #include <algorithm>
 
 #include "kaze_internal.h"
