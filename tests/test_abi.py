@@ -71,3 +71,20 @@ def test_host_only_entry_points_without_gpu(libkaze):
     good = kaze.default_options()
     assert L.kaze_create(ctypes.byref(good), 2, 64, None, ctypes.byref(h)) == kaze.ERR_INVALID_ARG
     L.kaze_destroy(None)
+
+
+def test_null_handles_are_rejected_without_gpu(libkaze):
+    """Every entry point that takes a handle returns KAZE_ERR_INVALID_ARG for a
+    NULL handle before touching the device (checked here on a machine with
+    no GPU): the streaming host detection, the fused FED steps, the FED
+    cycle and the single-step operators."""
+    from paper_1706_06750_gb300 import kaze
+    L = kaze.lib()
+    n = ctypes.c_int()
+    buf = (kaze.Keypoint * 4)()
+    taus = (ctypes.c_float * 2)(0.1, 0.2)
+    assert L.kaze_detect_host_next(None, None, None, 64, 64, 64, buf, 4, ctypes.byref(n)) == kaze.ERR_INVALID_ARG
+    assert L.kaze_detect_host(None, None, 64, 64, 64, buf, 4, ctypes.byref(n)) == kaze.ERR_INVALID_ARG
+    assert L.kaze_op_fed_steps(None, None, None, None, 64, 64, 64, taus, 2) == kaze.ERR_INVALID_ARG
+    assert L.kaze_op_fed_cycle(None, None, None, None, None, 64, 64, 64, 1.0, ctypes.byref(n)) == kaze.ERR_INVALID_ARG
+    assert L.kaze_op_conductance(None, None, None, 64, 64, 64, 0.02) == kaze.ERR_INVALID_ARG
