@@ -460,6 +460,9 @@ kaze_status kaze_surrogate_gradients(kaze_surrogate* s, const float* const* d_L,
 kaze_status kaze_surrogate_train_step(kaze_surrogate* s, const float* const* d_L, const float* const* d_g,
                                       const float* h_tau, const float* const* d_T, int n, int w, int h_,
                                       int pitch, float lr, double* h_loss);
+
+/* Number of Adam steps applied so far (restored by kaze_surrogate_load).
+ * KAZE_ERR_INVALID_ARG for a NULL surrogate or steps.  Host only. */
 kaze_status kaze_surrogate_steps_taken(const kaze_surrogate* s, long long* steps);
 
 /* Checkpoint: "KZSG", uint32 version 1, uint32 KAZE_SURROGATE_PARAMS,
