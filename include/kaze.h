@@ -113,8 +113,9 @@ void kaze_default_options(kaze_options* opt);
 /* Creates a handle for images up to max_w x max_h (3 <= max_w, max_h <= 4128:
  * each row and column is solved by 32 chunks whose coefficients must fit in
  * registers and shared memory).
- * Allocates all device buffers up front (about (2N + 3) * max_w * max_h * 4
- * bytes, plus 336 bytes per keypoint of max_keypoints).  cuda_stream: the
+ * Allocates all device buffers up front (about (2N + 4) * max_w * max_h * 4
+ * bytes -- levels, responses, conductance, row solution, two input planes
+ * -- plus 336 bytes per keypoint of max_keypoints).  cuda_stream: the
  * cudaStream_t all work goes to.  On error *out is NULL.  Errors:
  * INVALID_ARG (bad options or sizes), OOM, CUDA. */
 kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h,
