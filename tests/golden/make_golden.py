@@ -37,6 +37,32 @@ def main():
         json.dump(out, f, indent=1)
         f.write("\n")
 
+    # the same workload with the FED evolution (Eq. 5), and the orientation
+    # and M-SURF descriptor (Sec. II-C) of the AOS keypoints
+    from oracle import describe as od
+    fopt = oracle.Options.make(octaves=2, sublevels=4, scheme=oracle.SCHEME_FED)
+    flv, fD, fkp, fk = oracle.kaze_detect(img, fopt)
+    sig, _ = oracle.scale_table(2, 4, 1.6)
+    first = sorted(kp, key=lambda r: (int(r["level"]), int(r["iy"]), int(r["ix"])))[:12]
+    desc = []
+    for r in first:
+        a, d = od.describe_level(lv[int(r["level"])], float(sig[int(r["level"])]), [(float(r["x"]), float(r["y"]))])
+        desc.append([int(r["level"]), float(r["x"]), float(r["y"]), float(a[0])] + [float(v) for v in d[0]])
+    out2 = {
+        "workload": "256x256, 2 octaves x 4 sublevels, seed 1000",
+        "source": "oracle (FP64), written by tests/golden/make_golden.py",
+        "fed": {
+            "k": fk,
+            "level_mean": [float(x) for x in flv.reshape(flv.shape[0], -1).mean(axis=1)],
+            "level_checksum": [float(np.sum(flv[i] * flv[i])) for i in range(flv.shape[0])],
+            "keypoints": [[int(r["level"]), int(r["iy"]), int(r["ix"])] for r in fkp],
+        },
+        "describe": desc,
+    }
+    with open(os.path.join(HERE, "oracle_fed_describe_256x256.json"), "w") as f:
+        json.dump(out2, f, indent=1)
+        f.write("\n")
+
 
 if __name__ == "__main__":
     main()
