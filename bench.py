@@ -121,23 +121,34 @@ class ClockSampler:
 # --------------------------------------------------------------- roofline --
 
 def algorithmic_bytes(kind, pixels, n_levels, nbins=300):
-    """Minimum bytes a kernel kind must move in one detection (FP32 planes):
-    presmoothing reads I and writes L_0; the max pass reads L_0 and keeps
-    |grad|^2, which the histogram pass reads; each of
-    the N-1 steps writes g (read L), then its row and column halves each read
-    L and g and write (add) their half of L_i; the response reads and writes
-    every level, the extrema read every response once."""
+    """Minimum bytes a kernel kind must move in one detection (FP32 planes,
+    P pixels, N levels), from the method's data flow:
+      presmoothing       read I, write L_0                          8 P
+      contrast factor    two reads of L_0 (maximum, histogram)      8 P  (4 + 4)
+      each AOS step      pass A: read L_i-1, write g, write u_x    12 P
+                         pass B: read L_i-1, g, u_x, write L_i     16 P
+      detector response  read L_i, write DoH_i per level            8 P
+      extrema            read DoH_i once per level                  4 P
+    in all P (40 N - 12) bytes (628 P for N = 16).  The line kernels split
+    pass A into the conductance launch (read L, write g: 8 P) and the row
+    half (write u_x: 4 P); the column half is pass B (16 P); the resident
+    evolution takes all N - 1 steps in one launch (28 P each)."""
     steps = n_levels - 1
-    # the AOS halves each read L and g and add half of L_i
     table = {
-        "presmooth": 8, "grad_max": 8, "grad_hist": 4, "conductance": 8 * steps,
-        "aos_rows": 12 * steps, "aos_cols": 12 * steps, "doh": 8 * n_levels, "extrema": 4 * n_levels,
+        "presmooth": 8, "grad_max": 4, "grad_hist": 4, "conductance": 8 * steps,
+        "aos_rows": 4 * steps, "aos_cols": 16 * steps, "aos_evolve": 28 * steps,
+        "doh": 8 * n_levels, "extrema": 4 * n_levels,
     }
     if kind in table:
         return table[kind] * pixels
     if kind == "percentile":
         return 4 * nbins
     return 4
+
+
+def detection_bytes(pixels, n_levels):
+    """Algorithmic bytes of one whole detection: P (40 N - 12)."""
+    return pixels * (40 * n_levels - 12)
 
 
 # multiply-adds per pixel of the surrogate network: 3x3 taps x (5*32 + 32*32
@@ -171,6 +182,7 @@ KIND_SOURCES = {
     "percentile": ["k_filters.cu"], "conductance": ["k_filters.cu"],
     "aos_rows": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
     "aos_cols": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
+    "aos_evolve": ["k_evolve.cu"],
     "doh": ["k_detector.cu"], "extrema": ["k_detector.cu"], "describe": ["k_describe.cu"],
     "fed": ["k_fed.cu"],
 }
@@ -450,6 +462,8 @@ def run_ours(args, rank, world, local_rank):
                             "sample": f"{cores} processes, each the same centred {acw}x{ach} crop, "
                                       f"{asecs:.1f} s wall"}
 
+    whole_bytes = detection_bytes(pixels, OCTAVES * SUBLEVELS)
+    whole_gbs = whole_bytes / (t_dev_ms / args.steps * 1e-3) / 1e9
     value = whole_job_rate(world, args.steps, pixels, t_dev_ms)
     e2e = whole_job_rate(world, args.steps, pixels, t_e2e_ms)
     e2e_single = whole_job_rate(world, args.steps, pixels, t_single_ms)
@@ -471,7 +485,14 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches * args.steps,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes},
+                     "traffic": traffic,
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, one "
+                                        "single-kernel capture with cold caches (profiles/ncu_traffic.md); "
+                                        "null when the kernel changed since"),
+                     "algorithmic_bytes_per_launch": dom_bytes,
+                     "whole": {"algorithmic_bytes": whole_bytes, "ms": t_dev_ms / args.steps,
+                               "achieved": whole_gbs, "frac": whole_gbs / peak,
+                               "model": "P (40 N - 12) bytes: 628 B/px at N = 16"}},
         "kernels": kernels,
         "describe": describe,
         "fed": fed,

@@ -71,6 +71,18 @@ typedef enum {
                                         s_i = max(1, round(sigma_i)); single-
                                         image handles only                  */
 
+/* How the AOS steps of Eq. 4 are solved (the same method; the solutions
+ * agree to FP32 rounding). */
+#define KAZE_AOS_AUTO 0   /* the resident evolution when the image's 128 x 120
+                             tiles fit one per SM (at most 16 along a line) and
+                             sigma_d <= 1: all N-1 steps in one cooperative
+                             launch, each tile of L and g held in shared memory,
+                             lines solved in chunks coupled through their end
+                             values; the line kernels otherwise (default)      */
+#define KAZE_AOS_LINES 1  /* always the line kernels: per step a conductance
+                             pass, then every row and every column solved by
+                             one CTA strip each (no cooperative launch)         */
+
 /* Normalisation of the Hessian determinant, Eq. 8. */
 #define KAZE_DOH_SIGMA4 0         /* s_i^4 det, s_i = max(1, round(sigma_i)) (default) */
 #define KAZE_DOH_PAPER_LITERAL 1  /* (sigma_i / 2^o_i)^2 det, as Eq. 8 is printed      */
@@ -91,6 +103,7 @@ typedef struct kaze_options {
     int scheme;           /* KAZE_SCHEME_AOS (default) or KAZE_SCHEME_FED         */
     float fed_tau_max;    /* FED stability limit, (0, 0.25] (0.25)                */
     int extrema_window;   /* KAZE_EXTREMA_3X3 (default) or _SIGMA_WINDOW          */
+    int aos_solver;       /* KAZE_AOS_AUTO (default) or KAZE_AOS_LINES            */
 } kaze_options;
 
 /* One detected keypoint (Sec. II-B). */
@@ -135,6 +148,21 @@ kaze_status kaze_build_scale_space(kaze_handle* h, const float* d_img, int w, in
  * elements and its evolution time t_i.  Any output pointer may be NULL. */
 kaze_status kaze_get_level(kaze_handle* h, int i, const float** d_level,
                            int* pitch_elems, float* t_i);
+
+/* Test hook for failure detection of the resident AOS evolution
+ * (KAZE_AOS_AUTO): sets how many SM cycles one of its grid-barrier waits may
+ * take (0 restores the default, 2^31) and, if stall_tile >= 0, makes that
+ * tile never arrive at a barrier, so every wait runs out, the kernel returns
+ * early and the detection reports KAZE_ERR_TIMEOUT.  stall_tile < 0 clears
+ * the stall.  Drops the handle's recorded graphs. */
+kaze_status kaze_set_evolve_wait_limit(kaze_handle* h, long long cycles, int stall_tile);
+
+/* Scale of level i (0 <= i < N) from the handle's options, available
+ * without a build: sigma_i = sigma0 2^(o + s/S) of Eq. 6 (i = o S + s) and
+ * t_i = sigma_i^2 / 2 of Eq. 7, both as FP32 -- the values the kernels use
+ * (sigma_i sets the derivative step of Eq. 8 and the sampling of the
+ * descriptor).  Either output may be NULL.  INVALID_ARG for a bad index. */
+kaze_status kaze_get_level_scale(kaze_handle* h, int i, float* sigma_i, float* t_i);
 
 /* Contrast factor k used by the last build (synchronises the stream). */
 kaze_status kaze_get_contrast(kaze_handle* h, float* k);
@@ -363,16 +391,19 @@ void kaze_batch_destroy(kaze_batch* b);
  * internally lives in a file-scope device array that every GPU loading the
  * library holds until the process exits.  Limits: pitch * h <= 4,194,304
  * (16 MiB of scratch), 3 <= w, h <= 4128, pitch >= w and a multiple of 4,
- * all three buffers 16-byte aligned, d_Lnext distinct from the inputs;
- * anything else returns KAZE_ERR_INVALID_ARG before touching the GPU.
+ * all three buffers 16-byte aligned, d_Lnext overlapping neither input
+ * (each plane spans pitch * (h - 1) + w floats), cuda_stream belonging to
+ * the current device; anything else returns KAZE_ERR_INVALID_ARG before
+ * touching the GPU.
  * The first call on a device looks up the array's device address and sets
  * the kernels' shared-memory limits for the current device, so make that
- * first call before any stream capture.  All calls share the one array:
- * calls that overlap on the GPU (different streams, or another thread)
- * race on it and must be serialised by the caller.  Work goes to
- * cuda_stream (cudaStream_t); the call waits for it and returns
- * KAZE_ERR_TIMEOUT if a bounded device wait ran out, KAZE_ERR_CUDA on a
- * CUDA failure. */
+ * first call before any stream capture.  The address is kept for the life
+ * of the process: a cudaDeviceReset in between is not supported.  All calls
+ * share the one array: calls that overlap on the GPU (different streams, or
+ * another thread) race on it and must be serialised by the caller.
+ * The call is synchronous: its work goes to cuda_stream (cudaStream_t) and
+ * the call waits for that stream before it returns KAZE_OK,
+ * KAZE_ERR_TIMEOUT (a bounded device wait ran out) or KAZE_ERR_CUDA. */
 kaze_status kaze_aos_step_static(const float* d_Lprev, const float* d_g, float* d_Lnext, int pitch, int w,
                                  int h_, float tau, void* cuda_stream);
 

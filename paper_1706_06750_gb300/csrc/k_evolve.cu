@@ -1,0 +1,800 @@
+// k_evolve.cu -- the whole AOS evolution of Sec. II-A (levels 1..N-1, one
+// semi-implicit step of Eq. 4 per level, tau_i = t_i - t_{i-1} of Eq. 7) in
+// ONE persistent cooperative launch, with every tile of the image resident in
+// shared memory for all N-1 steps.
+//
+// The image is cut into tiles of TW x TH pixels, one CTA (one SM) per tile.
+// A CTA keeps its tile of L (with a HALO-pixel ring) and of the conductance
+// g (with a 1-pixel ring) in shared memory.  Per step:
+//   1. g = g2(|grad(G_sigma_d * L)|) of Eq. 2-3 on the tile and its ring,
+//      from the tile of L: a row-walking horizontal pass into a scratch
+//      tile, then column walkers for the vertical pass, the 3x3 Scharr pair
+//      (D = S(x+1) - S(x-1), E = 3 S(x-1) + 10 S(x) + 3 S(x+1), neighbours by
+//      warp shuffles) and g -- the operations of the line-kernel path, in
+//      the same order;
+//   2. every row and column of the tile is cut into chunks (8 per segment);
+//      each chunk's tridiagonal system, its couplings to the neighbouring
+//      chunks removed, is solved (Thomas) for its right-hand side and for
+//      the unit vectors at its two ends.  The ends of a chunk's solution
+//      then follow as  x = y - V x_left - W x_right  in its two external
+//      neighbours ("spike" form, as in the SPIKE algorithm of Polizzi &
+//      Sameh 2006);
+//   3. adjacent spike records merge into the record of their union (a 2x2
+//      solve at the joint); the 8 chunk records of a line segment merge into
+//      the segment's record, which goes to global memory;
+//   4. grid barrier; each line's thread reads the records of its line from
+//      every tile, merges those left and right of its own segment and solves
+//      for the segment's two external neighbours, then walks the chunk merges
+//      back to every chunk's external neighbours;
+//   5. each chunk is solved again with its external terms moved to the
+//      right-hand side: rows give u_x (shared memory), columns u_y and
+//      L_i = (u_x + u_y) / 2, written to the tile and to the level plane;
+//   6. grid barrier; the CTA reads the HALO ring of L_i from the level plane.
+// Borders: the lines have Neumann ends (no coupling past the image), every
+// stencil reflects coordinates into the image (half-sample symmetric).  Line
+// elements past the image inside a ragged tile are identity rows.
+//
+// Shared memory is laid out with odd row strides: the row solves give a lane
+// a row (lanes 32 rows apart in bank terms), the column solves a column.
+// Every grid-barrier wait is bounded; a timeout (or another CTA's) sets bit 0
+// of *status and the CTA returns.
+#include "kaze_internal.h"
+
+namespace kz {
+namespace ev {
+
+constexpr int TW = 128, TH = 120;  // tile
+constexpr int RMAX = 3;            // radius of G(sigma_d) this kernel takes
+constexpr int HALO = RMAX + 2;     // L ring: smoothing, Scharr, g ring
+constexpr int NT = 512, NWARP = NT / 32;
+constexpr int MR = 16, KR = TW / MR;  // row chunks: 8 of 16 elements
+constexpr int MC = 15, KC = TH / MC;  // column chunks: 8 of 15 elements
+constexpr int TMAX = 16;              // tiles along a line
+
+constexpr int LROWS = TH + 2 * HALO, LCOLS = TW + 2 * HALO, LS = LCOLS + 1;  // 130 x 138, stride 139
+constexpr int GROWS = TH + 2, GCOLS = TW + 2, GS = GCOLS + 1;                  // 122 x 130, stride 131
+constexpr int HROWS = LROWS, HCOLS = TW + 4, HS = HCOLS + 1;                   // 130 x 132, stride 133
+constexpr int US = TW + 1;                                                     // u_x, stride 129
+constexpr int REC = 6;
+constexpr int RREC = KR * REC * TH;  // row chunk records [k][f][r]
+constexpr int CREC = KC * REC * TW;  // column chunk records [k][f][c]
+constexpr int SROWS = TH + 4, SCOLS = TW + 4, SS = SCOLS + 1;  // smoothed S: 124 x 132, stride 133
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+// Shared memory: LH | A | XE | B.  During the conductance pass B holds the
+// horizontal pass H, A the smoothed S, and g is written into B (H is dead by
+// then); the line solves then use A for the chunk records, the staged
+// segment records (which also reach into XE) and u_x.
+constexpr int OFF_L = 0;
+constexpr int OFF_A = (OFF_L + LROWS * LS + 3) & ~3;
+constexpr int A_SIZE = cmax(cmax(SROWS * SS, TH * US), RREC + CREC);
+constexpr int OFF_X = OFF_A + A_SIZE;
+constexpr int X_SIZE = KR * 2 * TH + KC * 2 * TW;  // chunk externals
+constexpr int OFF_B = OFF_X + X_SIZE;
+constexpr int B_SIZE = cmax(HROWS * HS, GROWS * GS);
+constexpr int SMEM_FLOATS = OFF_B + B_SIZE;
+constexpr size_t SMEM_BYTES = (size_t)SMEM_FLOATS * sizeof(float);
+static_assert((OFF_A * 4) % 16 == 0, "the staging copies land on a 16-byte boundary");
+static_assert(SMEM_BYTES <= 227 * 1024, "tile state must fit one SM's shared memory");
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* q) { return (unsigned)__cvta_generic_to_shared(q); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Waits for phase `parity` of `bar`, giving up after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit)
+{
+    const long long t0 = clock64();
+    while (true) {
+        unsigned ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+// Spike record of a block of consecutive line elements: its first and last
+// unknowns as  x = y - V x_left - W x_right  in the block's two external
+// neighbours.
+struct Rec {
+    float yF, VF, WF, yL, VL, WL;
+};
+// One unknown in the same form.
+struct Pt {
+    float y, V, W;
+};
+
+// Union of adjacent blocks A (left) and B (right).  P and Q receive A's last
+// and B's first unknowns in terms of the union's external neighbours.
+__device__ __forceinline__ Rec merge(const Rec& A, const Rec& B, Pt& P, Pt& Q)
+{
+    // the joint: xA_l + WA_l xB_f = yA_l - VA_l xl,  VB_f xA_l + xB_f = yB_f - WB_f xr
+    const float s = rcp_approx(fmaf(-A.WL, B.VF, 1.f));
+    P.y = s * fmaf(-A.WL, B.yF, A.yL);
+    P.V = s * A.VL;
+    P.W = -s * (A.WL * B.WF);
+    Q.y = s * fmaf(-B.VF, A.yL, B.yF);
+    Q.V = -s * (B.VF * A.VL);
+    Q.W = s * B.WF;
+    Rec M;
+    M.yF = fmaf(-A.WF, Q.y, A.yF);
+    M.VF = fmaf(-A.WF, Q.V, A.VF);
+    M.WF = -(A.WF * Q.W);
+    M.yL = fmaf(-B.VL, P.y, B.yL);
+    M.VL = -(B.VL * P.V);
+    M.WL = fmaf(-B.VL, P.W, B.WL);
+    return M;
+}
+
+__device__ __forceinline__ Rec merge(const Rec& A, const Rec& B)
+{
+    Pt P, Q;
+    return merge(A, B, P, Q);
+}
+
+__device__ __forceinline__ float eval(const Pt& p, float xl, float xr) { return p.y - p.V * xl - p.W * xr; }
+
+// One chunk of M consecutive elements of a line (Eq. 4 with the AOS
+// splitting): c_i = -tau (g_i + g_i+1) couples element i to i+1, a_i = c_i-1,
+// b_i = 1 - a_i - c_i.  The conductance past the image holds ghost values
+// (+-g of the last pixel, alternating) that make every coupling across the
+// image border exactly zero, so elements past the border are decoupled rows
+// and the chunk needs no masks.
+template <int M>
+struct Chunk {
+    // d[i * ds]: right-hand side, g[i * gs]: conductance (g[-gs], g[M * gs]:
+    // the neighbours' values)
+    const float* d;
+    const float* g;
+    int ds, gs;
+    float tau;
+
+    // Thomas on the chunk with its couplings a_0, c_M-1 removed, for the
+    // right-hand side d (dl, dr subtracted at the first / last element) and,
+    // if wanted, for e_0.
+    template <bool WANT_V>
+    __device__ __forceinline__ void factor(float (&q)[M], float (&dy)[M], float (&dv)[M], float dl, float dr,
+                                           float& a0, float& clast, float& rlast) const
+    {
+        float gc = g[0];
+        a0 = -tau * (g[-gs] + gc);
+        float a = a0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const float gn = g[(i + 1) * gs];
+            const float c = -tau * (gc + gn);
+            const float b = 1.f - a - c;
+            float di = d[i * ds];
+            if (i == 0) di -= dl;
+            if (i == M - 1) {
+                di -= dr;
+                clast = c;
+            }
+            float r;
+            if (i == 0) {
+                r = rcp_approx(b);
+                dy[0] = di * r;
+                if (WANT_V) dv[0] = r;
+            } else {
+                r = rcp_approx(fmaf(-a, q[i - 1], b));
+                dy[i] = fmaf(-a, dy[i - 1], di) * r;
+                if (WANT_V) dv[i] = -a * dv[i - 1] * r;
+            }
+            q[i] = c * r;
+            if (i == M - 1) rlast = r;
+            a = c;
+            gc = gn;
+        }
+    }
+
+    // The chunk's spike record.
+    __device__ __forceinline__ Rec record() const
+    {
+        float q[M], dy[M], dv[M];
+        float a0, cl, rl;
+        factor<true>(q, dy, dv, 0.f, 0.f, a0, cl, rl);
+        float y = dy[M - 1], v = dv[M - 1];
+#pragma unroll
+        for (int i = M - 2; i >= 0; --i) {
+            y = fmaf(-q[i], y, dy[i]);
+            v = fmaf(-q[i], v, dv[i]);
+        }
+        // (A^-1)_{0,M-1} = (A^-1)_{M-1,0} = dv[M-1]: the chunk matrix is symmetric
+        Rec R;
+        R.yF = y;
+        R.VF = a0 * v;
+        R.WF = cl * dv[M - 1];
+        R.yL = dy[M - 1];
+        R.VL = a0 * dv[M - 1];
+        R.WL = cl * rl;
+        return R;
+    }
+
+    // The chunk's solution given its external neighbours; x[i] receives
+    // element i.
+    __device__ __forceinline__ void solve(float xl, float xr, float (&x)[M]) const
+    {
+        float q[M], dv[M];
+        float a0, cl, rl;
+        // the external terms a_0 xl and c_M-1 xr move to the right-hand side
+        const float a0v = -tau * (g[-gs] + g[0]);
+        const float clv = -tau * (g[(M - 1) * gs] + g[M * gs]);
+        factor<false>(q, x, dv, a0v * xl, clv * xr, a0, cl, rl);
+#pragma unroll
+        for (int i = M - 2; i >= 0; --i) x[i] = fmaf(-q[i], x[i + 1], x[i]);
+    }
+};
+
+struct Params {
+    float* levels;    // N planes of pitch * h floats, plane stride `plane`
+    long long plane;
+    int pitch, w, h, n_levels;
+    int tiles_x, tiles_y;
+    const float* d_k;  // contrast factor
+    float wt[RMAX + 1];  // G(sigma_d) taps for offsets 0..RMAX (0 past the radius)
+    int diffusivity;
+    float tau[kMaxLevels];
+    float* xrow;  // row segment records [y][tiles_x][6]
+    float* xcol;  // column segment records [x][tiles_y][6] (16-byte aligned)
+    unsigned int* barrier;
+    int* status;
+    long long wait_limit;  // SM cycles a grid-barrier wait may take
+    int stall_tile;        // test hook: this tile never arrives (-1: none)
+};
+
+// Grid-wide barrier in two halves: every CTA arrives once per barrier, and
+// `target` is the count once every CTA has arrived.  The wait is bounded: on
+// timeout, or when another CTA has already flagged one, it sets bit 0 of
+// *status and returns false.
+__device__ __forceinline__ void grid_arrive(const Params& p)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if ((int)blockIdx.x != p.stall_tile) atomicAdd(p.barrier, 1u);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait(const Params& p, unsigned target, volatile int* s_abort)
+{
+    if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        while (ld_acquire(p.barrier) < target) {
+            if (ld_relaxed(p.status) != 0 || clock64() - t0 > p.wait_limit) {
+                atomicOr(p.status, 1);
+                *s_abort = 1;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    return *s_abort == 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(const Params& p, unsigned target, volatile int* s_abort)
+{
+    grid_arrive(p);
+    return grid_wait(p, target, s_abort);
+}
+
+// Copies n elements from global to shared memory: element e goes from
+// src(e) to dst(e).  Loads are issued in batches of B before their stores
+// (the cache-global loads are ordered asm statements).
+template <int B, typename Src, typename Dst>
+__device__ __forceinline__ void copy_batched(int n, Src src, Dst dst)
+{
+    for (int e0 = threadIdx.x; e0 < n; e0 += B * NT) {
+        float v[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int e = e0 + b * NT;
+            v[b] = e < n ? __ldcg(src(e)) : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int e = e0 + b * NT;
+            if (e < n) *dst(e) = v[b];
+        }
+    }
+}
+
+// Every LH position (r, c), r in [-HALO, TH + HALO), c in [-HALO, TW + HALO),
+// from plane `src` at the reflected image position.
+__device__ __forceinline__ void load_all(float* LH, const float* src, const Params& p, int x0, int y0)
+{
+    copy_batched<8>(
+        LROWS * LCOLS,
+        [&](int e) {
+            const int rr = e / LCOLS, cc = e - rr * LCOLS;
+            return src + (size_t)reflect_index(y0 + rr - HALO, p.h) * p.pitch + reflect_index(x0 + cc - HALO, p.w);
+        },
+        [&](int e) {
+            const int rr = e / LCOLS, cc = e - rr * LCOLS;
+            return LH + rr * LS + cc;
+        });
+}
+
+// The LH positions outside the tile's own image pixels [0, th) x [0, tw):
+// the bands above and below (whole width), then left and right of them.
+__device__ __forceinline__ void load_halo(float* LH, const float* src, const Params& p, int x0, int y0, int tw,
+                                          int th)
+{
+    const int nb = TH + HALO - th;  // rows below
+    const int wr = TW + HALO - tw;  // columns right of the image part
+    const int nside = HALO + wr;
+    const int n1 = (HALO + nb) * LCOLS;
+    auto pos = [&](int e, int& rr, int& cc) {
+        if (e < n1) {
+            const int q = e / LCOLS;
+            cc = e - q * LCOLS;
+            rr = q < HALO ? q : th + HALO + (q - HALO);
+        } else {
+            const int f = e - n1, r = f / nside, q = f - r * nside;
+            rr = r + HALO;
+            cc = q < HALO ? q : tw + HALO + (q - HALO);
+        }
+    };
+    copy_batched<8>(
+        n1 + th * nside,
+        [&](int e) {
+            int rr, cc;
+            pos(e, rr, cc);
+            return src + (size_t)reflect_index(y0 + rr - HALO, p.h) * p.pitch + reflect_index(x0 + cc - HALO, p.w);
+        },
+        [&](int e) {
+            int rr, cc;
+            pos(e, rr, cc);
+            return LH + rr * LS + cc;
+        });
+}
+
+// Ghost conductance past the image (see Chunk): along rows, columns
+// x >= w take (-1)^(x - w + 1) g(w - 1) and x = -1 takes -g(0); along
+// columns the same with y.  Runs after the conductance pass; the two
+// directions in turn (their writes meet only at unused corners).
+__device__ __forceinline__ void ghost_conductance(float* G, int x0, int y0, int w, int h)
+{
+    const int cw = w - x0, rh = h - y0;  // first tile column / row past the image
+    if (x0 == 0)
+        for (int rr = threadIdx.x; rr < GROWS; rr += NT) G[rr * GS] = -G[rr * GS + 1];
+    if (cw <= TW) {
+        const int nc = TW + 1 - cw;  // ghost columns cw .. TW (index c + 1)
+        for (int e = threadIdx.x; e < GROWS * nc; e += NT) {
+            const int rr = e / nc, c = cw + (e - rr * nc);
+            float* row = G + rr * GS;
+            row[c + 1] = ((c - cw) & 1) ? row[cw] : -row[cw];  // row[cw]: column cw - 1
+        }
+    }
+    __syncthreads();
+    if (y0 == 0)
+        for (int cc = threadIdx.x; cc < GCOLS; cc += NT) G[cc] = -G[GS + cc];
+    if (rh <= TH) {
+        const int nr = TH + 1 - rh;  // ghost rows rh .. TH (index r + 1)
+        for (int e = threadIdx.x; e < nr * GCOLS; e += NT) {
+            const int q = e / GCOLS, cc = e - q * GCOLS, r = rh + q;
+            G[(r + 1) * GS + cc] = ((r - rh) & 1) ? G[rh * GS + cc] : -G[rh * GS + cc];
+        }
+    }
+}
+
+// g of Eq. 2-3 on tile rows -1..TH, columns -1..TW (into G) from LH in three
+// passes: the horizontal Gaussian pass H(r, c) = sum_j w_j L(r, c + j),
+// r in [-HALO, TH + HALO), c in [-2, TW + 2), by threads walking 44 columns
+// of one row (lanes: consecutive rows) ...
+__device__ __forceinline__ void h_pass(const float* __restrict__ LH, float* __restrict__ H, const Params& p)
+{
+    const float w0 = p.wt[0], w1 = p.wt[1], w2 = p.wt[2], w3 = p.wt[3];
+    constexpr int SEG = HCOLS / 3;
+    static_assert(SEG * 3 == HCOLS && HROWS * 3 <= NT, "three row segments, one job a thread");
+    for (int job = threadIdx.x; job < HROWS * 3; job += NT) {
+        const int s = job / HROWS, rr = job - s * HROWS;
+        const int cb = -2 + SEG * s;
+        const float* src = LH + rr * LS + (cb + HALO);
+        float* dst = H + rr * HS + (cb + 2);
+        float v0 = src[-3], v1 = src[-2], v2 = src[-1], v3 = src[0], v4 = src[1], v5 = src[2];
+#pragma unroll 4
+        for (int q = 0; q < SEG; ++q) {
+            const float v6 = src[q + 3];
+            float hv = w0 * v3;
+            hv = fmaf(w1, v2 + v4, hv);
+            hv = fmaf(w2, v1 + v5, hv);
+            hv = fmaf(w3, v0 + v6, hv);
+            dst[q] = hv;
+            v0 = v1;
+            v1 = v2;
+            v2 = v3;
+            v3 = v4;
+            v4 = v5;
+            v5 = v6;
+        }
+    }
+}
+
+// ... then the vertical pass S, r in [-2, TH + 2), c in [-2, TW + 2), by
+// threads walking 42 rows of one column with the 7 H values in registers
+// (lanes: consecutive columns) ...
+__device__ __forceinline__ void v_pass(const float* __restrict__ H, float* __restrict__ S, const Params& p)
+{
+    const float w0 = p.wt[0], w1 = p.wt[1], w2 = p.wt[2], w3 = p.wt[3];
+    constexpr int RG = (SROWS + 2) / 3;  // 42 rows a job
+    static_assert(SCOLS * 3 <= NT, "one job a thread");
+    for (int job = threadIdx.x; job < SCOLS * 3; job += NT) {
+        const int q = job / SCOLS, c = job - q * SCOLS;  // c: column + 2
+        const int r0 = q * RG, r1 = min(r0 + RG, SROWS);  // S rows r0 - 2 .. r1 - 3
+        // S row index i needs H row indices i .. i + 6
+        const float* h = H + c;
+        float h0 = h[(r0 + 0) * HS], h1 = h[(r0 + 1) * HS], h2 = h[(r0 + 2) * HS], h3 = h[(r0 + 3) * HS],
+              h4 = h[(r0 + 4) * HS], h5 = h[(r0 + 5) * HS];
+        float* o = S + c;
+#pragma unroll 4
+        for (int i = r0; i < r1; ++i) {
+            const float h6 = h[(i + 6) * HS];
+            float sv = w0 * h3;
+            sv = fmaf(w1, h2 + h4, sv);
+            sv = fmaf(w2, h1 + h5, sv);
+            sv = fmaf(w3, h0 + h6, sv);
+            o[i * SS] = sv;
+            h0 = h1;
+            h1 = h2;
+            h2 = h3;
+            h3 = h4;
+            h4 = h5;
+            h5 = h6;
+        }
+    }
+}
+
+// ... and the 3x3 Scharr pair and g (Eq. 3) at rows -1..TH, columns -1..TW:
+// a thread walks 41 rows of one column with the D, E values of the rows
+// above in registers (the operations of the line-kernel path, in order).
+template <bool G1>
+__device__ __forceinline__ void scharr_pass(const float* __restrict__ S, float* __restrict__ G, float inv_k2)
+{
+    constexpr int RG = (GROWS + 2) / 3;  // 41 rows a job
+    static_assert(GCOLS * 3 <= NT, "one job a thread");
+    for (int job = threadIdx.x; job < GCOLS * 3; job += NT) {
+        const int q = job / GCOLS, cc = job - q * GCOLS;  // cc: column + 1
+        const int r0 = q * RG, r1 = min(r0 + RG, GROWS);  // g rows r0 - 1 .. r1 - 2
+        // g row gr (index gr + 1) uses S rows gr - 1 .. gr + 1 (index gr + 1 .. gr + 3)
+        const float* sc = S + cc;  // S column (cc - 1) - 1 + 2 = cc: the left neighbour
+        auto de = [&](int si, float& d, float& e) {
+            const float sl = sc[si * SS], sv = sc[si * SS + 1], sr = sc[si * SS + 2];
+            d = sr - sl;
+            e = fmaf(10.f, sv, 3.f * (sl + sr));
+        };
+        float dm, em, d0, e0;
+        de(r0, dm, em);
+        de(r0 + 1, d0, e0);
+        float* o = G + cc;
+#pragma unroll 4
+        for (int i = r0; i < r1; ++i) {
+            float dp, ep;
+            de(i + 2, dp, ep);
+            const float lx = fmaf(10.f, d0, 3.f * (dm + dp)) * (1.f / 32.f);
+            const float ly = (ep - em) * (1.f / 32.f);
+            const float m2 = fmaf(ly, ly, lx * lx);
+            o[i * GS] = G1 ? expf(-(m2 * inv_k2)) : __fdividef(1.f, fmaf(m2, inv_k2, 1.f));
+            dm = d0;
+            d0 = dp;
+            em = e0;
+            e0 = ep;
+        }
+    }
+}
+
+__device__ __forceinline__ Rec load_rec(const float* s, int st)
+{
+    return Rec{s[0 * st], s[1 * st], s[2 * st], s[3 * st], s[4 * st], s[5 * st]};
+}
+
+__device__ __forceinline__ void store_rec(float* d, int st, const Rec& R)
+{
+    d[0 * st] = R.yF;
+    d[1 * st] = R.VF;
+    d[2 * st] = R.WF;
+    d[3 * st] = R.yL;
+    d[4 * st] = R.VL;
+    d[5 * st] = R.WL;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params p)
+{
+    extern __shared__ __align__(16) float sm[];
+    float* LH = sm + OFF_L;
+    float* SC = sm + OFF_A;  // S, then chunk records, staged records, u_x
+    float* XE = sm + OFF_X;
+    float* G = sm + OFF_B;   // H, then g
+    float* RRc = SC;         // row chunk records [k][f][r]
+    float* CRc = SC + RREC;  // column chunk records [k][f][c]
+    float* XR = XE;          // row chunk externals [k][2][r]
+    float* XC = XE + KR * 2 * TH;
+    __shared__ int s_abort;
+    __shared__ __align__(8) uint64_t s_bar;  // completion of the record staging copies
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = blockIdx.x % p.tiles_x, ty = blockIdx.x / p.tiles_x;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int tw = min(TW, p.w - x0), th = min(TH, p.h - y0);
+    const unsigned ntiles = gridDim.x;
+    unsigned nbar = 0;
+    if (tid == 0) {
+        s_abort = 0;
+        mbar_init(&s_bar);
+    }
+    const float kk = *p.d_k;
+    const float inv_k2 = 1.f / (kk * kk);
+    // lines: threads 0..TH-1 own the tile's rows, threads 128..128+TW-1 its columns
+    const bool row_line = tid < th;
+    const bool col_line = tid >= 128 && tid - 128 < tw;
+    const int li = row_line ? tid : tid - 128;
+
+    load_all(LH, p.levels, p, x0, y0);
+    __syncthreads();
+
+    for (int lev = 1; lev < p.n_levels; ++lev) {
+        const float tau = p.tau[lev];
+        float* Lout = p.levels + (size_t)lev * p.plane;
+
+        // 1. conductance of L_{lev-1} on the tile and its ring, ghosts past
+        // the image
+        h_pass(LH, G, p);
+        __syncthreads();
+        v_pass(G, SC, p);
+        __syncthreads();
+        if (p.diffusivity == KAZE_G1)
+            scharr_pass<true>(SC, G, inv_k2);
+        else
+            scharr_pass<false>(SC, G, inv_k2);
+        __syncthreads();
+        ghost_conductance(G, x0, y0, p.w, p.h);
+        __syncthreads();
+
+        // 2. chunk records (warp jobs: 32 lines x one chunk)
+        for (int job = warp; job < 4 * KR + 4 * KC; job += NWARP) {
+            if (job < 4 * KR) {
+                const int r = (job / KR) * 32 + lane, k = job % KR;
+                if (r < th) {
+                    const Chunk<MR> ch{LH + (r + HALO) * LS + (k * MR + HALO), G + (r + 1) * GS + (k * MR + 1), 1,
+                                       1, tau};
+                    store_rec(RRc + (k * REC) * TH + r, TH, ch.record());
+                }
+            } else {
+                const int jb = job - 4 * KR;
+                const int c = (jb / KC) * 32 + lane, k = jb % KC;
+                if (c < tw) {
+                    const Chunk<MC> ch{LH + (k * MC + HALO) * LS + (c + HALO), G + (k * MC + 1) * GS + (c + 1), LS,
+                                       GS, tau};
+                    store_rec(CRc + (k * REC) * TW + c, TW, ch.record());
+                }
+            }
+        }
+        __syncthreads();
+
+        // 3. segment records (one thread per line) to global memory; the
+        // joints of the chunk merges stay in registers for step 4
+        Pt P[8], Q[8];
+        if (row_line || col_line) {
+            const float* src = row_line ? RRc + li : CRc + li;
+            const int st = row_line ? TH : TW;
+            Rec S = load_rec(src, st);
+#pragma unroll
+            for (int k = 1; k < 8; ++k) S = merge(S, load_rec(src + k * REC * st, st), P[k], Q[k]);
+            float* dst = row_line ? p.xrow + ((size_t)(y0 + li) * p.tiles_x + tx) * REC
+                                  : p.xcol + ((size_t)(x0 + li) * p.tiles_y + ty) * REC;
+            store_rec(dst, 1, S);
+        }
+        nbar += ntiles;
+        if (!grid_barrier(p, nbar, &s_abort)) return;
+
+        // 4. the records of the tile's lines from every tile (rows, then
+        // columns: two contiguous blocks of global memory), staged into shared
+        // memory by two bulk copies
+        const int nrow = th * p.tiles_x * REC, ncol = tw * p.tiles_y * REC;
+        const int nrow4 = (nrow + 3) & ~3;
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const unsigned brow = (unsigned)nrow4 * 4u, bcol = (unsigned)((ncol + 3) & ~3) * 4u;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_bar)),
+                         "r"(brow + bcol)
+                         : "memory");
+            bulk_load(SC, p.xrow + (size_t)y0 * p.tiles_x * REC, brow, &s_bar);
+            bulk_load(SC + nrow4, p.xcol + (size_t)x0 * p.tiles_y * REC, bcol, &s_bar);
+        }
+        if (!__syncthreads_and(mbar_wait(&s_bar, (unsigned)(lev - 1) & 1u, p.wait_limit))) {
+            if (tid == 0) {
+                atomicOr(p.status, 1);
+                mbar_wait(&s_bar, (unsigned)(lev - 1) & 1u, p.wait_limit);  // copies still in flight
+            }
+            __syncthreads();
+            return;
+        }
+        // the line's own segment: merge the records left and right of it and
+        // solve for its two external neighbours
+        float xl = 0.f, xr = 0.f;
+        if (row_line || col_line) {
+            const int T = row_line ? p.tiles_x : p.tiles_y;
+            const int t = row_line ? tx : ty;
+            const float* rs = SC + (row_line ? li * T * REC : nrow4 + li * T * REC);
+            Rec Lb = load_rec(rs, 1), Rb = Lb;
+            for (int s = 1; s < t; ++s) Lb = merge(Lb, load_rec(rs + s * REC, 1));
+            if (t + 1 < T) Rb = load_rec(rs + (t + 1) * REC, 1);
+            for (int s = t + 2; s < T; ++s) Rb = merge(Rb, load_rec(rs + s * REC, 1));
+            const Rec own = load_rec(rs + t * REC, 1);
+            Pt P1{0.f, 0.f, 0.f}, Q1;
+            Rec Mx = own;
+            if (t > 0) Mx = merge(Lb, own, P1, Q1);
+            if (t + 1 < T) {
+                Pt P2, Q2;
+                merge(Mx, Rb, P2, Q2);
+                xr = Q2.y;
+            }
+            if (t > 0) xl = P1.y - P1.W * xr;
+        }
+        __syncthreads();  // the staged records are dead: XE is written next
+        // every chunk's external neighbours, walking the chunk joints back
+        // from the segment's right end
+        if (row_line || col_line) {
+            float* xe = row_line ? XR + li : XC + li;
+            const int st = row_line ? TH : TW;
+            float right = xr;
+#pragma unroll
+            for (int k = 7; k >= 1; --k) {
+                const float first_k = eval(Q[k], xl, right);
+                xe[(k * 2 + 0) * st] = eval(P[k], xl, right);
+                xe[(k * 2 + 1) * st] = right;
+                right = first_k;
+            }
+            xe[0] = xl;
+            xe[st] = right;
+        }
+        __syncthreads();
+
+        // 5a. row chunks with their externals: u_x into SC
+        float* U = SC;
+        for (int job = warp; job < 4 * KR; job += NWARP) {
+            const int r = (job / KR) * 32 + lane, k = job % KR;
+            if (r < th) {
+                const Chunk<MR> ch{LH + (r + HALO) * LS + (k * MR + HALO), G + (r + 1) * GS + (k * MR + 1), 1, 1, tau};
+                float x[MR];
+                ch.solve(XR[(k * 2 + 0) * TH + r], XR[(k * 2 + 1) * TH + r], x);
+                float* u = U + r * US + k * MR;
+#pragma unroll
+                for (int i = 0; i < MR; ++i) u[i] = x[i];
+            }
+        }
+        __syncthreads();
+        // 5b. column chunks: L = (u_x + u_y) / 2 into the tile and the level plane
+        for (int job = warp; job < 4 * KC; job += NWARP) {
+            const int c = (job / KC) * 32 + lane, k = job % KC;
+            if (c < tw) {
+                const Chunk<MC> ch{LH + (k * MC + HALO) * LS + (c + HALO), G + (k * MC + 1) * GS + (c + 1), LS, GS,
+                                   tau};
+                float x[MC];
+                ch.solve(XC[(k * 2 + 0) * TW + c], XC[(k * 2 + 1) * TW + c], x);
+#pragma unroll
+                for (int i = 0; i < MC; ++i) {
+                    const int r = k * MC + i;
+                    const float v = 0.5f * (U[r * US + c] + x[i]);
+                    LH[(r + HALO) * LS + (c + HALO)] = v;
+                    if (r < th) Lout[(size_t)(y0 + r) * p.pitch + (x0 + c)] = v;
+                }
+            }
+        }
+        if (lev + 1 < p.n_levels) {
+            // 6. every tile's L_lev is in the level plane: read the ring
+            nbar += ntiles;
+            if (!grid_barrier(p, nbar, &s_abort)) return;
+            load_halo(LH, Lout, p, x0, y0, tw, th);
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace ev
+
+cudaError_t configure_evolve_kernel()
+{
+    return cudaFuncSetAttribute(ev::k_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ev::SMEM_BYTES);
+}
+
+size_t evolve_exchange_floats(int max_tiles)
+{
+    // segment records of every line of every tile (rows, then columns from a
+    // 16-byte boundary), and slack for the 16-byte rounding of the copies
+    return (size_t)(ev::TH + ev::TW) * max_tiles * ev::REC + 64;
+}
+
+bool evolve_fits(int w, int h, int radius, int* tiles)
+{
+    if (radius < 1 || radius > ev::RMAX) return false;
+    const int tx = (w + ev::TW - 1) / ev::TW, ty = (h + ev::TH - 1) / ev::TH;
+    if (tx > ev::TMAX || ty > ev::TMAX) return false;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ev::k_evolve, ev::NT, ev::SMEM_BYTES) != cudaSuccess)
+        return false;
+    if (per_sm < 1 || tx * ty > sms * per_sm) return false;
+    if (tiles) *tiles = tx * ty;
+    return true;
+}
+
+cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int h, int n_levels, const double* t,
+                          const float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
+                          unsigned int* barrier, int* status, cudaStream_t st, long long wait_limit,
+                          int stall_tile)
+{
+    int tiles = 0;
+    if (!evolve_fits(w, h, taps.r, &tiles) || tiles > max_tiles || n_levels > kMaxLevels) return cudaErrorInvalidValue;
+    ev::Params p;
+    p.levels = levels;
+    p.plane = plane;
+    p.pitch = pitch;
+    p.w = w;
+    p.h = h;
+    p.n_levels = n_levels;
+    p.tiles_x = (w + ev::TW - 1) / ev::TW;
+    p.tiles_y = (h + ev::TH - 1) / ev::TH;
+    p.d_k = d_k;
+    for (int j = 0; j <= ev::RMAX; ++j) p.wt[j] = j <= taps.r ? taps.w[taps.r + j] : 0.f;
+    p.diffusivity = diffusivity;
+    for (int i = 0; i < kMaxLevels; ++i) p.tau[i] = (i >= 1 && i < n_levels) ? (float)(t[i] - t[i - 1]) : 0.f;
+    p.xrow = exchange;
+    p.xcol = exchange + (((size_t)h * p.tiles_x * ev::REC + 3) & ~(size_t)3);
+    p.barrier = barrier;
+    p.status = status;
+    p.wait_limit = wait_limit > 0 ? wait_limit : (1ll << 31);
+    p.stall_tile = stall_tile;
+    cudaError_t e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiles);
+    cfg.blockDim = dim3(ev::NT);
+    cfg.dynamicSmemBytes = ev::SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ev::k_evolve, p);
+}
+
+}  // namespace kz

@@ -25,11 +25,12 @@ namespace {
 // Kernel kinds, in pipeline order, for launch counting and profiling.
 enum KernelKind {
     KK_PRESMOOTH = 0, KK_GRAD_MAX, KK_GRAD_HIST, KK_PERCENTILE, KK_SET_SCALAR,
-    KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_SURROGATE, KK_DESCRIBE, KK_FED, KK_COUNT
+    KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_SURROGATE, KK_DESCRIBE, KK_FED, KK_EVOLVE,
+    KK_COUNT
 };
 const char* const kKindNames[KK_COUNT] = {
     "presmooth", "grad_max", "grad_hist", "percentile", "set_scalar",
-    "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate", "describe", "fed"};
+    "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate", "describe", "fed", "aos_evolve"};
 }  // namespace
 
 struct kaze_handle {
@@ -55,6 +56,11 @@ struct kaze_handle {
     unsigned int* d_hist = nullptr;
     unsigned int* d_count = nullptr;
     int* d_status = nullptr;         // bit 0: a bounded device wait ran out
+    float* d_exchange = nullptr;     // segment records of the resident evolution
+    unsigned int* d_barrier = nullptr;  // its grid-barrier counter
+    int max_tiles = 0;               // tiles the exchange buffer serves (the SM count)
+    long long evolve_wait_limit = 0;  // test hook of the resident evolution's barrier waits
+    int evolve_stall_tile = -1;
     kaze_keypoint* d_kp = nullptr;
     kaze_keypoint* d_dkp = nullptr;  // keypoints uploaded for description
     float* d_desc = nullptr;         // their descriptors, max_keypoints x 64
@@ -265,6 +271,18 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
                       kz::launch_conductance(Lp, h->g, zero, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
         return KAZE_OK;
     };
+    if (h->N > 1 && !h->surrogate && h->opt.scheme == KAZE_SCHEME_AOS && h->opt.aos_solver == KAZE_AOS_AUTO &&
+        h->d_exchange && kz::evolve_fits(w, hh, h->tapsd.r, nullptr)) {
+        // every AOS step in one cooperative launch, the tiles resident in
+        // shared memory
+        KZ_LAUNCH(h, KK_EVOLVE,
+                  kz::launch_evolve(h->levels, h->cur_plane, P, w, hh, h->N, h->t, h->d_k, h->tapsd,
+                                    h->opt.diffusivity, h->d_exchange, h->max_tiles, h->d_barrier, h->d_status, st,
+                                    h->evolve_wait_limit, h->evolve_stall_tile));
+        h->built = true;
+        h->responded = false;
+        return KAZE_OK;
+    }
     for (int i = 1; i < h->N; ++i) {
         const float* Lp = level_ptr(h, i - 1);
         float* Li = level_ptr(h, i);
@@ -488,6 +506,7 @@ KAZE_API void kaze_default_options(kaze_options* o)
     o->scheme = KAZE_SCHEME_AOS;
     o->fed_tau_max = 0.25f;
     o->extrema_window = KAZE_EXTREMA_3X3;
+    o->aos_solver = KAZE_AOS_AUTO;
 }
 
 KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, void* cuda_stream,
@@ -514,6 +533,8 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
         return create_fail(KAZE_ERR_INVALID_ARG, "fed_tau_max must lie in (0, 0.25]");
     if (o.extrema_window != KAZE_EXTREMA_3X3 && o.extrema_window != KAZE_EXTREMA_SIGMA_WINDOW)
         return create_fail(KAZE_ERR_INVALID_ARG, "unknown extrema window");
+    if (o.aos_solver != KAZE_AOS_AUTO && o.aos_solver != KAZE_AOS_LINES)
+        return create_fail(KAZE_ERR_INVALID_ARG, "unknown AOS solver");
     if (max_w < 3 || max_h < 3 || max_w > 16384 || max_h > 16384)
         return create_fail(KAZE_ERR_INVALID_ARG, "max_w and max_h must be in 3..16384");
     if (kz::aos_rows_smem_bytes(max_w) == 0 || kz::aos_cols_smem_bytes(max_h) == 0)
@@ -573,6 +594,10 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
             ce = kz::configure_fed_kernels();
             what = "configure_fed_kernels";
         }
+        if (ce == cudaSuccess) {
+            ce = kz::configure_evolve_kernel();
+            what = "configure_evolve_kernel";
+        }
         if (ce != cudaSuccess) {
             delete h;
             return create_fail(KAZE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(ce) + " " +
@@ -597,6 +622,10 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     const size_t off_kp = bytes;     bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
     const size_t off_dkp = bytes;    bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
     const size_t off_desc = bytes;   bytes += al(sizeof(float) * 64 * (size_t)o.max_keypoints);
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t off_xchg = bytes;   bytes += al(sizeof(float) * kz::evolve_exchange_floats(sms));
+    const size_t off_bar = bytes;    bytes += al(sizeof(unsigned int));
     cudaError_t e = cudaMalloc(&h->arena, bytes);
     if (e != cudaSuccess) {
         delete h;
@@ -618,6 +647,9 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     h->d_kp = (kaze_keypoint*)(a + off_kp);
     h->d_dkp = (kaze_keypoint*)(a + off_dkp);
     h->d_desc = (float*)(a + off_desc);
+    h->d_exchange = sms > 0 ? (float*)(a + off_xchg) : nullptr;
+    h->d_barrier = (unsigned int*)(a + off_bar);
+    h->max_tiles = sms;
     e = cudaMallocHost(&h->h_count, 2 * sizeof(unsigned int));
     if (e != cudaSuccess) {
         cudaFree(h->arena);
@@ -663,6 +695,25 @@ KAZE_API kaze_status kaze_get_level(kaze_handle* h, int i, const float** d_level
     if (d_level) *d_level = level_ptr(h, i);
     if (pitch_elems) *pitch_elems = h->cur_pitch;
     if (t_i) *t_i = (float)h->t[i];
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_set_evolve_wait_limit(kaze_handle* h, long long cycles, int stall_tile)
+{
+    if (!h) return KAZE_ERR_INVALID_ARG;
+    if (cycles < 0) return fail(h, KAZE_ERR_INVALID_ARG, "negative wait limit");
+    h->evolve_wait_limit = cycles;
+    h->evolve_stall_tile = stall_tile < 0 ? -1 : stall_tile;
+    drop_graph(h);  // recorded graphs hold the old launch parameters
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_get_level_scale(kaze_handle* h, int i, float* sigma_i, float* t_i)
+{
+    if (!h) return KAZE_ERR_INVALID_ARG;
+    if (i < 0 || i >= h->N) return fail(h, KAZE_ERR_INVALID_ARG, "level index out of range");
+    if (sigma_i) *sigma_i = h->tab.sigma[i];  // Eq. 6, the value the kernels use
+    if (t_i) *t_i = (float)h->t[i];          // Eq. 7
     return KAZE_OK;
 }
 
@@ -978,8 +1029,16 @@ KAZE_API kaze_status kaze_op_aos_step(kaze_handle* h, const float* d_Lprev, cons
     if (pitch < w || pitch % 4) return fail(h, KAZE_ERR_INVALID_ARG, "pitch must be >= w and a multiple of 4");
     const uintptr_t al = (uintptr_t)d_Lprev | (uintptr_t)d_g | (uintptr_t)d_ux | (uintptr_t)d_Lnext;
     if (al & 15) return fail(h, KAZE_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
-    if (d_Lnext == d_Lprev || d_Lnext == d_g || d_ux == d_Lprev || d_ux == d_g)
-        return fail(h, KAZE_ERR_INVALID_ARG, "outputs alias inputs");
+    {
+        // planes span pitch * (h - 1) + w floats: no output may overlap an
+        // input or the other output anywhere (the column pass writes while
+        // it still reads)
+        const size_t span = sizeof(float) * ((size_t)pitch * (hh - 1) + w);
+        if (kz::ranges_overlap(d_Lnext, d_Lprev, span) || kz::ranges_overlap(d_Lnext, d_g, span) ||
+            kz::ranges_overlap(d_ux, d_Lprev, span) || kz::ranges_overlap(d_ux, d_g, span) ||
+            kz::ranges_overlap(d_ux, d_Lnext, span))
+            return fail(h, KAZE_ERR_INVALID_ARG, "outputs overlap inputs");
+    }
     if (!(tau >= 0.f)) return fail(h, KAZE_ERR_INVALID_ARG, "negative tau");
     KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
     KZ_TRY(h, kz::launch_aos_rows(d_Lprev, d_g, d_ux, nullptr, pitch, w, hh, tau, h->d_status, h->stream));

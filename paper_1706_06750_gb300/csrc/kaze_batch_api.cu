@@ -181,6 +181,7 @@ kaze_status prepare_branches(kaze_batch* b)
     const int mh = *std::max_element(b->h.begin(), b->h.end());
     kaze_options o = b->opt;
     o.max_keypoints = 1;  // keypoints go to the batch's own buffers
+    o.aos_solver = KAZE_AOS_LINES;  // branches run side by side: no launch may claim every SM
     for (int i = 0; i < nb; ++i) {
         cudaStream_t st = nullptr;
         KB_TRY(b, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));

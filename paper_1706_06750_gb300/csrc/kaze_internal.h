@@ -43,6 +43,13 @@ struct DescTable {
     int step[kMaxLevels];
 };
 
+// True when the byte ranges [a, a + bytes) and [b, b + bytes) intersect.
+inline bool ranges_overlap(const void* a, const void* b, size_t bytes)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bytes && y < x + bytes;
+}
+
 // Half-sample symmetric reflection of i into [0, n).
 __host__ __device__ __forceinline__ int reflect_index(int i, int n)
 {
@@ -144,6 +151,22 @@ cudaError_t launch_aos_cols(const float* L, const float* g, const float* ux, flo
                             int pitch, int w, int h, float tau, int* d_status, cudaStream_t st, int cols = 0);
 size_t aos_rows_smem_bytes(int w);
 size_t aos_cols_smem_bytes(int h);
+
+// The whole AOS evolution (levels 1..n_levels-1 from level 0) in one
+// cooperative launch with each 128 x 120 tile resident in shared memory
+// (k_evolve.cu).  evolve_fits: whether a w x h image with a gradient
+// smoothing radius `radius` can take it on the current device (tiles one per
+// SM); `exchange` holds evolve_exchange_floats(max_tiles) floats, `barrier`
+// one counter; a timed-out grid barrier sets bit 0 of *status.  wait_limit:
+// SM cycles a barrier wait may take (0: 2^31); stall_tile >= 0 (a test
+// hook) makes that tile never arrive, so every wait runs out.
+cudaError_t configure_evolve_kernel();
+size_t evolve_exchange_floats(int max_tiles);
+bool evolve_fits(int w, int h, int radius, int* tiles);
+cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int h, int n_levels, const double* t,
+                          const float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
+                          unsigned int* barrier, int* status, cudaStream_t st, long long wait_limit = 0,
+                          int stall_tile = -1);
 
 // Detector response of Eq. 8 for levels [l0, l0 + nl) of a level stack.
 // Number of kernels launch_doh issues for levels l0 .. l0 + nl - 1.

@@ -22,7 +22,7 @@ constexpr int kMaxDevices = 64;
 // Row-solution scratch and the status word of the bounded device waits,
 // shared by every call on a device.
 static __device__ __align__(256) float g_static_ux[kStaticMaxPixels];
-static __device__ __align__(256) int g_static_status[64];
+static __device__ __align__(256) int g_static_status[1];
 
 struct DeviceScratch {
     bool ready = false;
@@ -33,7 +33,9 @@ DeviceScratch g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
 // First use on a device (which must be current): device addresses of the
-// file-scope arrays and the kernels' shared-memory limits.
+// file-scope arrays and the kernels' shared-memory limits.  The addresses are
+// cached per device ordinal for the life of the process; a cudaDeviceReset
+// invalidates them and is not supported.
 kaze_status setup_current_device(DeviceScratch** out)
 {
     int dev = 0;
@@ -60,12 +62,21 @@ KAZE_API kaze_status kaze_aos_step_static(const float* d_Lprev, const float* d_g
     if ((long long)pitch * h > kStaticMaxPixels) return KAZE_ERR_INVALID_ARG;
     if (kz::aos_rows_smem_bytes(w) == 0 || kz::aos_cols_smem_bytes(h) == 0) return KAZE_ERR_INVALID_ARG;
     if (((uintptr_t)d_Lprev | (uintptr_t)d_g | (uintptr_t)d_Lnext) & 15) return KAZE_ERR_INVALID_ARG;
-    if (d_Lnext == d_Lprev || d_Lnext == d_g) return KAZE_ERR_INVALID_ARG;
+    // the planes span pitch * (h - 1) + w floats; the output may not overlap
+    // either input anywhere (the column pass writes while it still reads)
+    const size_t span = sizeof(float) * ((size_t)pitch * (h - 1) + w);
+    if (kz::ranges_overlap(d_Lnext, d_Lprev, span) || kz::ranges_overlap(d_Lnext, d_g, span))
+        return KAZE_ERR_INVALID_ARG;
     if (!(tau >= 0.f)) return KAZE_ERR_INVALID_ARG;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    // the scratch address belongs to the current device: the stream must too
+    int cur = 0, sdev = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(stream, &sdev) != cudaSuccess)
+        return KAZE_ERR_CUDA;
+    if (sdev != cur) return KAZE_ERR_INVALID_ARG;
     DeviceScratch* s = nullptr;
     const kaze_status st = setup_current_device(&s);
     if (st != KAZE_OK) return st;
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
     // the array keeps the previous call's contents: the status word must
     // start at zero, the row solution is overwritten before it is read
     if (cudaMemsetAsync(s->status, 0, sizeof(int), stream) != cudaSuccess) return KAZE_ERR_CUDA;

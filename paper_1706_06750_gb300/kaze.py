@@ -30,6 +30,8 @@ SCHEME_AOS = 0
 SCHEME_FED = 1
 EXTREMA_3X3 = 0
 EXTREMA_SIGMA_WINDOW = 1
+AOS_AUTO = 0
+AOS_LINES = 1
 
 
 class KazeError(RuntimeError):
@@ -55,6 +57,7 @@ class Options(ctypes.Structure):
         ("scheme", ctypes.c_int),
         ("fed_tau_max", ctypes.c_float),
         ("extrema_window", ctypes.c_int),
+        ("aos_solver", ctypes.c_int),
     ]
 
 
@@ -94,6 +97,8 @@ _SIGNATURES = {
     "kaze_set_stream": (_i, [_vp, _vp]),
     "kaze_build_scale_space": (_i, [_vp, _vp, _i, _i, _i]),
     "kaze_get_level": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_f)]),
+    "kaze_get_level_scale": (_i, [_vp, _i, ctypes.POINTER(_f), ctypes.POINTER(_f)]),
+    "kaze_set_evolve_wait_limit": (_i, [_vp, ctypes.c_longlong, _i]),
     "kaze_get_contrast": (_i, [_vp, ctypes.POINTER(_f)]),
     "kaze_detector_response": (_i, [_vp]),
     "kaze_get_response": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
@@ -332,9 +337,16 @@ class Kaze:
 
     def level_sigma(self, i):
         """sigma_i of level i as the library holds it (Eq. 6, FP32)."""
-        o = self.options
-        oc, sub = divmod(int(i), o.sublevels)
-        return float(np.float32(float(np.float32(o.sigma0)) * 2.0 ** (oc + sub / o.sublevels)))
+        s = _f()
+        self._ck(self._L.kaze_get_level_scale(self._h, int(i), ctypes.byref(s), None), "kaze_get_level_scale")
+        return float(s.value)
+
+    def set_evolve_wait_limit(self, cycles, stall_tile=-1):
+        """Failure-detection hook of the resident evolution: a grid-barrier
+        wait gives up after `cycles`; stall_tile >= 0 makes that tile never
+        arrive (kaze_set_evolve_wait_limit)."""
+        self._ck(self._L.kaze_set_evolve_wait_limit(self._h, int(cycles), int(stall_tile)),
+                 "kaze_set_evolve_wait_limit")
 
     def level_time(self, i):
         t = _f()

@@ -137,7 +137,11 @@ def test_pipeline_describe_on_oracle_scale_space(kz):
             sel = kps["level"] == lev
             a1, d1 = k.op_describe(k.level(lev, copy=False), k.level_sigma(lev), kps[sel])
             assert np.array_equal(d1, desc[sel]) and np.array_equal(a1, out["angle"][sel].astype(np.float64))
-    sig, _ = oracle.scale_table(2, 4, s0)
+    sig, t = oracle.scale_table(2, 4, s0)
+    with kz.Kaze(w, h, octaves=2, sublevels=4) as k:
+        # the scale table the library reports (Eq. 6-7) is the oracle's, rounded once to FP32
+        for lev in range(8):
+            assert k.level_sigma(lev) == float(np.float32(sig[lev]))
     agree, n = 0, 0
     for lev in sorted(set(int(v) for v in kps["level"])):
         sel = np.nonzero(kps["level"] == lev)[0]
