@@ -2,8 +2,10 @@
 
 One step = one whole detection of one 1920x1200 float32 image (4 octaves x 4
 sublevels): presmoothing, contrast factor, 15 AOS steps, the detector
-response of all 16 levels and the 3x3x3 extrema with the keypoints copied to
-the host -- kaze_detect through the C ABI, replaying its recorded CUDA graph.
+response of all 16 levels and the 3x3x3 extrema with the keypoint count and
+slots copied to the host -- kaze_detect_enqueue through the C ABI, replaying
+its recorded CUDA graph (kaze_detect_collect, the host's wait and sort,
+follows each step's end event).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -48,6 +50,7 @@ W_IMG, H_IMG = 1920, 1200
 OCTAVES, SUBLEVELS = 4, 4
 WORKLOAD = "1920x1200 float32 image, 4 octaves x 4 sublevels, scale space + detector response + extrema"
 L2_FLUSH_BYTES = 256 << 20
+KEYPOINT_SLOTS = 4096  # keypoints a detection copies to the host with the count
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -132,11 +135,14 @@ def algorithmic_bytes(kind, pixels, n_levels, nbins=300):
     in all P (40 N - 12) bytes (628 P for N = 16).  The line kernels split
     pass A into the conductance launch (read L, write g: 8 P) and the row
     half (write u_x: 4 P); the column half is pass B (16 P); the resident
-    evolution takes all N - 1 steps in one launch (28 P each)."""
+    evolution takes all N - 1 steps in one launch (28 P each), and with the
+    presmoothing and the contrast factor inside it (front_evolve) also their
+    8 P + 8 P."""
     steps = n_levels - 1
     table = {
         "presmooth": 8, "grad_max": 4, "grad_hist": 4, "conductance": 8 * steps,
         "aos_rows": 4 * steps, "aos_cols": 16 * steps, "aos_evolve": 28 * steps,
+        "front_evolve": 8 + 8 + 28 * steps,
         "doh": 8 * n_levels, "extrema": 4 * n_levels,
     }
     if kind in table:
@@ -183,7 +189,8 @@ KIND_SOURCES = {
     "aos_rows": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
     "aos_cols": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
     "aos_evolve": ["k_evolve.cu"],
-    "doh": ["k_detector.cu"], "extrema": ["k_detector.cu"], "describe": ["k_describe.cu"],
+    "front_evolve": ["k_evolve.cu"],
+    "doh": ["k_detector.cu", "doh_walk.cuh"], "extrema": ["k_detector.cu"], "describe": ["k_describe.cu"],
     "fed": ["k_fed.cu"],
 }
 
@@ -372,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
     n_kp = len(k.detect(x))
     launches = k.last_launch_count()
 
-    def timed(fn):
+    def timed(fn, after=None):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         with torch.cuda.stream(stream):
@@ -381,6 +388,8 @@ def run_ours(args, rank, world, local_rank):
                 starts[i].record(stream)
                 fn()
                 ends[i].record(stream)
+                if after is not None:
+                    after()
         torch.cuda.synchronize()
         return sum(s.elapsed_time(e) for s, e in zip(starts, ends))
 
@@ -388,7 +397,10 @@ def run_ours(args, rank, world, local_rank):
     clocks.start()
     time.sleep(0.3)
     barrier()
-    t_dev_ms = timed(lambda: k.detect(x))
+    # the device's time for a whole detection: the recorded detection with
+    # the count and keypoint slots copied to the host; the host's wait and
+    # sort (kaze_detect_collect) follow the end event
+    t_dev_ms = timed(lambda: k.detect_enqueue(x), after=k.detect_collect)
     barrier()
     t_single_ms = timed(lambda: k.detect_host(pinned))
     barrier()
@@ -478,7 +490,9 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": pixels * 4,
-                "d2h_bytes_per_step": 4 + 40 * n_kp,
+                # count and status, the keypoint slots copied with them, and
+                # a second copy only when there are more keypoints than slots
+                "d2h_bytes_per_step": 8 + 40 * KEYPOINT_SLOTS + (40 * n_kp if n_kp > KEYPOINT_SLOTS else 0),
                 "api": "kaze_detect_host_next (pinned host images; each step copies the next step's image "
                        "during its detection and reads its keypoints back)",
                 "single": {"value": e2e_single, "unit": UNIT, "api": "kaze_detect_host (copy, then detect)"}},

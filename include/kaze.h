@@ -186,9 +186,22 @@ kaze_status kaze_find_extrema(kaze_handle* h, kaze_keypoint* h_out, int capacity
  * device image.  The fixed launch sequence is recorded once per image size
  * and input pointer as a CUDA graph and replayed afterwards; on the legacy
  * or per-thread default stream, which cannot be captured, the same kernels
- * are launched one by one.  Synchronises the stream. */
+ * are launched one by one.  Synchronises the stream.  The keypoint count
+ * travels to the host with the first min(4096, max_keypoints) keypoint slots
+ * (40 bytes each, in one copy), so a detection with no more keypoints than
+ * that takes one round trip; more take a second copy. */
 kaze_status kaze_detect(kaze_handle* h, const float* d_img, int w, int h_, int pitch_elems,
                         kaze_keypoint* h_out, int capacity, int* count);
+
+/* kaze_detect in two halves, so that the host can work while the GPU
+ * detects: kaze_detect_enqueue replays the recorded detection (with the
+ * count and the keypoint slots copied to pinned host memory) on the handle's
+ * stream and returns without waiting; kaze_detect_collect waits for it and
+ * fills h_out, capacity and count as kaze_detect does.  Every enqueue must be
+ * collected before the handle's next build or detection (STATE otherwise);
+ * collect without an enqueue returns KAZE_ERR_STATE. */
+kaze_status kaze_detect_enqueue(kaze_handle* h, const float* d_img, int w, int h_, int pitch_elems);
+kaze_status kaze_detect_collect(kaze_handle* h, kaze_keypoint* h_out, int capacity, int* count);
 
 /* kaze_detect on a HOST image: copies h_img to the device on the handle's
  * stream, runs the pipeline, copies the keypoints back.  For overlap the

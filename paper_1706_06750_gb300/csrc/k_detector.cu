@@ -15,73 +15,35 @@
 // Borders reflect coordinates into the image (half-sample symmetric).
 //
 // GB300 mapping: one launch for a group of levels (grid.z), no shared
-// memory.  A thread owns one column x and walks WK consecutive lattice rows
-// y = py + s k of one residue py of the level's step s.  Its five column taps
-// x - 2s .. x + 2s are reflected once; each lattice row costs five loads
-// (coalesced across the warp, L1/L2-resident) and the three horizontal
-// filters, and each output then combines five consecutive lattice rows held
-// in registers: ~(WK + 4) / WK x 5 loads and ~30 FP32 operations per output.
-#include "kaze_internal.h"
+// memory.  A thread owns one column x and walks DOH_WK consecutive lattice
+// rows y = py + s k of one residue py of the level's step s (doh_walk.cuh).
+// Its five column taps x - 2s .. x + 2s are reflected once; each lattice row
+// costs five loads (coalesced across the warp, L1/L2-resident) and the three
+// horizontal filters, and each output then combines five consecutive lattice
+// rows held in registers: ~(WK + 4) / WK x 5 loads and ~30 FP32 operations
+// per output.
+#include "doh_walk.cuh"
 
 namespace kz {
 namespace {
 
-constexpr int WK = 24;        // outputs per thread (consecutive lattice rows)
-constexpr int WTX = 128;      // threads per CTA (consecutive columns)
-constexpr int DPD = 4;        // lattice rows of loads kept in flight
+constexpr int WTX = 128;  // threads per CTA (consecutive columns)
 
 // blockIdx.y = py * nseg + seg for the level's step s: residue py, segment
-// seg of WK lattice rows; blocks past the level's residues return.
+// seg of DOH_WK lattice rows; blocks past the level's residues return.
 __global__ void __launch_bounds__(WTX)
 k_doh(const float* __restrict__ L, float* __restrict__ D, int pitch, long long plane_stride, int w, int h,
       int l0, const __grid_constant__ LevelTable tab)
 {
     const int level = l0 + blockIdx.z;
     const int s = tab.step[level];
-    const int nseg = ((h + s - 1) / s + WK - 1) / WK;
+    const int nseg = doh_segments(h, s);
     const int py = blockIdx.y / nseg, seg = blockIdx.y - py * nseg;
     const int x = blockIdx.x * WTX + threadIdx.x;
-    const int k0 = seg * WK;
+    const int k0 = seg * DOH_WK;
     if (py >= s || x >= w || py + s * k0 >= h) return;
-    const float scale = tab.doh_scale[level];
-    L += (size_t)level * plane_stride;
-    D += (size_t)level * plane_stride;
-    int cx[5];
-#pragma unroll
-    for (int a = 0; a < 5; ++a) cx[a] = reflect_index(x + (a - 2) * s, w);
-    // lattice rows k0 - 2 .. k0 + WK + 1 of residue py: loads run DPD rows
-    // ahead of the filters; the last five filtered rows stay in registers
-    constexpr int NM = WK + 4;
-    // element offsets within the level plane fit 32 bits: loads and the
-    // store index from one 64-bit base each
-    float buf[DPD + 1][5];
-#pragma unroll
-    for (int m = 0; m < DPD; ++m) {
-        const int ro = reflect_index(py + s * (k0 + m - 2), h) * pitch;
-#pragma unroll
-        for (int a = 0; a < 5; ++a) buf[m][a] = __ldg(L + (unsigned)(ro + cx[a]));
-    }
-    float hd[5], hs[5], hx[5];
-#pragma unroll
-    for (int m = 0; m < NM; ++m) {
-        if (m + DPD < NM) {
-            const int ro = reflect_index(py + s * (k0 + m + DPD - 2), h) * pitch;
-#pragma unroll
-            for (int a = 0; a < 5; ++a) buf[(m + DPD) % (DPD + 1)][a] = __ldg(L + (unsigned)(ro + cx[a]));
-        }
-        const float* v = buf[m % (DPD + 1)];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            hd[q] = hd[q + 1];
-            hs[q] = hs[q + 1];
-            hx[q] = hx[q + 1];
-        }
-        doh_lattice_row(v[0], v[1], v[2], v[3], v[4], hd[4], hs[4], hx[4]);
-        if (m < 4) continue;
-        const int y = py + s * (k0 + m - 4);
-        if (y >= h) break;
-        D[(unsigned)(y * pitch + x)] = doh_value(hd, hs, hx, scale);
-    }
+    doh_walk(L + (size_t)level * plane_stride, D + (size_t)level * plane_stride, pitch, w, h, s,
+             tab.doh_scale[level], x, py, k0, [](const float* q) { return __ldg(q); });
 }
 
 // Each thread tests 4 adjacent pixels (one 16-byte load) of one row of
@@ -185,7 +147,7 @@ cudaError_t launch_doh(const float* L, float* D, int pitch, long long plane_stri
     for (int i = l0; i < l0 + nl; ++i) {
         const int s = tab.step[i];
         if (s < 1 || s > 4096) return cudaErrorInvalidValue;
-        const int nseg = ((h + s - 1) / s + WK - 1) / WK;
+        const int nseg = doh_segments(h, s);
         gy = s * nseg > gy ? s * nseg : gy;
     }
     if (gy > 65535) return cudaErrorInvalidValue;

@@ -74,6 +74,14 @@ constexpr int B_SIZE = cmax(HROWS * HS, GROWS * GS);
 constexpr int SMEM_FLOATS = OFF_B + B_SIZE;
 constexpr size_t SMEM_BYTES = (size_t)SMEM_FLOATS * sizeof(float);
 static_assert((OFF_A * 4) % 16 == 0, "the staging copies land on a 16-byte boundary");
+// Presmoothing inside the launch (radius R0MAX): the input tile over LH and A,
+// the row pass over XE and B.
+constexpr int R0MAX = 5;
+constexpr int IS = TW + 2 * (HALO + R0MAX) + 1;  // staged input, stride 149
+constexpr int PS = LCOLS + 1;                     // row pass, stride 139
+constexpr int OFF_I = OFF_L, OFF_P = OFF_X;
+static_assert((TH + 2 * (HALO + R0MAX)) * IS <= OFF_X, "the staged input fits LH and A");
+static_assert(OFF_P + (TH + 2 * (HALO + R0MAX)) * PS <= SMEM_FLOATS, "the row pass fits XE and B");
 static_assert(SMEM_BYTES <= 227 * 1024, "tile state must fit one SM's shared memory");
 
 __device__ __forceinline__ float rcp_approx(float x)
@@ -268,7 +276,7 @@ struct Params {
     long long plane;
     int pitch, w, h, n_levels;
     int tiles_x, tiles_y;
-    const float* d_k;  // contrast factor
+    float* d_k;  // contrast factor (read, or written when computed here)
     float wt[RMAX + 1];  // G(sigma_d) taps for offsets 0..RMAX (0 past the radius)
     int diffusivity;
     float tau[kMaxLevels];
@@ -276,6 +284,17 @@ struct Params {
     float* xcol;  // column segment records [x][tiles_y][6] (16-byte aligned)
     unsigned int* barrier;
     int* status;
+    // presmoothing inside the launch (img != null): the input image and the
+    // Gaussian taps w[0 .. 2 r0] of offsets -r0 .. r0; level 0 is written here
+    const float* img;
+    int img_pitch, r0;
+    float pw[2 * R0MAX + 1];
+    // contrast factor inside the launch (hist != null): maximum and histogram
+    // of the interior gradient magnitudes of step 1, percentile; k to d_k
+    unsigned int* hmax_bits;
+    unsigned int* hist;
+    int nbins;
+    double pct;
     long long wait_limit;  // SM cycles a grid-barrier wait may take
     int stall_tile;        // test hook: this tile never arrives (-1: none)
 };
@@ -313,6 +332,19 @@ __device__ __forceinline__ bool grid_barrier(const Params& p, unsigned target, v
 {
     grid_arrive(p);
     return grid_wait(p, target, s_abort);
+}
+
+// Asynchronous 4-byte copy from global to shared memory (cp.async); a
+// cp_async_wait_all makes this thread's copies complete.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // Copies n elements from global to shared memory: element e goes from
@@ -485,11 +517,18 @@ __device__ __forceinline__ void v_pass(const float* __restrict__ H, float* __res
 // ... and the 3x3 Scharr pair and g (Eq. 3) at rows -1..TH, columns -1..TW:
 // a thread walks 41 rows of one column with the D, E values of the rows
 // above in registers (the operations of the line-kernel path, in order).
-template <bool G1>
-__device__ __forceinline__ void scharr_pass(const float* __restrict__ S, float* __restrict__ G, float inv_k2)
+// MODE_G2 / MODE_G1 write g of Eq. 3; MODE_M2 writes |grad|^2 and returns
+// this thread's maximum of |grad| over the tile's own interior image pixels
+// (the contrast factor's maximum pass).
+enum { MODE_G2 = 0, MODE_G1 = 1, MODE_M2 = 2 };
+
+template <int MODE>
+__device__ __forceinline__ float scharr_pass(const float* __restrict__ S, float* __restrict__ G, float inv_k2, int x0,
+                                             int y0, int tw, int th, int w, int h)
 {
     constexpr int RG = (GROWS + 2) / 3;  // 41 rows a job
     static_assert(GCOLS * 3 <= NT, "one job a thread");
+    float mx = 0.f;
     for (int job = threadIdx.x; job < GCOLS * 3; job += NT) {
         const int q = job / GCOLS, cc = job - q * GCOLS;  // cc: column + 1
         const int r0 = q * RG, r1 = min(r0 + RG, GROWS);  // g rows r0 - 1 .. r1 - 2
@@ -504,6 +543,10 @@ __device__ __forceinline__ void scharr_pass(const float* __restrict__ S, float* 
         de(r0, dm, em);
         de(r0 + 1, d0, e0);
         float* o = G + cc;
+        // interior image pixels of the tile's own column, if any (MODE_M2)
+        const int gc = cc - 1, gx = x0 + gc;
+        const bool col_in = gc >= 0 && gc < tw && gx >= 1 && gx <= w - 2;
+        const int ilo = max(1 - y0, 0) + 1, ihi = min(h - 2 - y0, th - 1) + 1;  // g row index range
 #pragma unroll 4
         for (int i = r0; i < r1; ++i) {
             float dp, ep;
@@ -511,13 +554,133 @@ __device__ __forceinline__ void scharr_pass(const float* __restrict__ S, float* 
             const float lx = fmaf(10.f, d0, 3.f * (dm + dp)) * (1.f / 32.f);
             const float ly = (ep - em) * (1.f / 32.f);
             const float m2 = fmaf(ly, ly, lx * lx);
-            o[i * GS] = G1 ? expf(-(m2 * inv_k2)) : __fdividef(1.f, fmaf(m2, inv_k2, 1.f));
+            if (MODE == MODE_M2) {
+                o[i * GS] = m2;
+                if (col_in && i >= ilo && i <= ihi) mx = fmaxf(mx, sqrtf(m2));
+            } else {
+                o[i * GS] = MODE == MODE_G1 ? expf(-(m2 * inv_k2)) : __fdividef(1.f, fmaf(m2, inv_k2, 1.f));
+            }
             dm = d0;
             d0 = dp;
             em = e0;
             e0 = ep;
         }
     }
+    return mx;
+}
+
+// The Gaussian presmoothing of Sec. III-1 of the input image on the tile and
+// its HALO ring into LH, the operations of the presmoothing kernel in order
+// (rows first, taps accumulated left to right from zero, reflected input):
+// the input tile with an R0 + HALO ring is staged in shared memory (over LH
+// and A), the row pass goes into P (over XE and B) by threads walking 46
+// columns of one row, then the column pass into LH by threads walking 44 rows
+// of one column, each with the 11 inputs in registers.  Positions outside the
+// image then take the value of their reflection (the half-sample symmetric
+// extension of L_0), and the tile's own pixels go to the level plane.
+__device__ __forceinline__ void presmooth_tile(float* __restrict__ sm, const Params& p, int x0, int y0, int tw,
+                                               int th, float* __restrict__ L0)
+{
+    constexpr int R0 = R0MAX, IR = TH + 2 * (HALO + R0), IC = TW + 2 * (HALO + R0);
+    float* I = sm + OFF_I;
+    float* P = sm + OFF_P;
+    float* LH = sm + OFF_L;
+    // every copy in flight at once: one round trip to memory
+    for (int rr = threadIdx.x >> 5; rr < IR; rr += NWARP) {
+        const float* in = p.img + (size_t)reflect_index(y0 + rr - HALO - R0, p.h) * p.img_pitch;
+        for (int cc = threadIdx.x & 31; cc < IC; cc += 32)
+            cp_async4(I + rr * IS + cc, in + reflect_index(x0 + cc - HALO - R0, p.w));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    float wj[2 * R0 + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * R0; ++j) wj[j] = p.pw[j];
+    // row pass: P(r, c) for rows -HALO - R0 .. TH + HALO + R0 - 1, columns
+    // -HALO .. TW + HALO - 1 (three walks of 46 columns a row, unrolled: the
+    // window shifts by register renaming)
+    static_assert(3 * 46 == LCOLS && 3 * 44 >= LROWS, "walk lengths");
+    for (int job = threadIdx.x; job < IR * 3; job += NT) {
+        const int sg = job / IR, rr = job - sg * IR;
+        const float* in = I + rr * IS + 46 * sg;  // P column c reads staged columns c .. c + 2 R0
+        float* dst = P + rr * PS + 46 * sg;
+        float v[46 + 2 * R0];
+#pragma unroll
+        for (int j = 0; j < 46 + 2 * R0; ++j) v[j] = in[j];
+#pragma unroll
+        for (int c = 0; c < 46; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j <= 2 * R0; ++j) acc = fmaf(wj[j], v[c + j], acc);
+            dst[c] = acc;
+        }
+    }
+    __syncthreads();
+    // column pass: L_0(r, c) for rows -HALO .. TH + HALO - 1 into LH (over the
+    // dead input tile), three walks of up to 44 rows a column
+    for (int job = threadIdx.x; job < LCOLS * 3; job += NT) {
+        const int sg = job / LCOLS, cc = job - sg * LCOLS;
+        const int rb = 44 * sg, n = min(44, LROWS - rb);  // LH row index; P row index + j
+        const float* col = P + rb * PS + cc;
+        float v[2 * R0 + 1];
+#pragma unroll
+        for (int j = 0; j < 2 * R0; ++j) v[j + 1] = col[j * PS];
+#pragma unroll
+        for (int r = 0; r < 44; ++r) {
+            if (r < n) {
+#pragma unroll
+                for (int j = 0; j < 2 * R0; ++j) v[j] = v[j + 1];
+                v[2 * R0] = col[(r + 2 * R0) * PS];
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j <= 2 * R0; ++j) acc = fmaf(wj[j], v[j], acc);
+                LH[(rb + r) * LS + cc] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    // the reflected extension past the image, from positions inside it.
+    // Every position the stencils of image pixels reach lies within four
+    // pixels of the border and reflects into this tile's window; positions
+    // farther out (deep in a ragged tile) only feed ghost conductances and
+    // decoupled line elements, and take 0 when their reflection falls
+    // outside the window (any finite value serves).  Positions past the image
+    // lie in the rows above -y0 and from h - y0 on, and in the columns left
+    // of -x0 and from w - x0 on.
+    const int rin0 = max(0, HALO - y0), rin1 = min(LROWS, p.h - y0 + HALO);  // LH rows inside the image
+    const int cin0 = max(0, HALO - x0), cin1 = min(LCOLS, p.w - x0 + HALO);
+    auto fill = [&](int rr, int cc) {
+        const int sy = reflect_index(y0 + rr - HALO, p.h) - y0 + HALO;
+        const int sx = reflect_index(x0 + cc - HALO, p.w) - x0 + HALO;
+        LH[rr * LS + cc] = (sy >= 0 && sy < LROWS && sx >= 0 && sx < LCOLS) ? LH[sy * LS + sx] : 0.f;
+    };
+    const int nout_r = rin0 + (LROWS - rin1);  // whole rows outside
+    for (int e = threadIdx.x; e < nout_r * LCOLS; e += NT) {
+        const int q = e / LCOLS, cc = e - q * LCOLS;
+        fill(q < rin0 ? q : rin1 + (q - rin0), cc);
+    }
+    const int nout_c = cin0 + (LCOLS - cin1);  // columns outside, on the rows inside
+    for (int e = threadIdx.x; e < (rin1 - rin0) * nout_c; e += NT) {
+        const int r = rin0 + e / nout_c, q = e % nout_c;
+        fill(r, q < cin0 ? q : cin1 + (q - cin0));
+    }
+    // own pixels to the level plane
+    for (int e = threadIdx.x; e < th * tw; e += NT) {
+        const int r = e / tw, c = e - r * tw;
+        L0[(size_t)(y0 + r) * p.pitch + x0 + c] = LH[(r + HALO) * LS + (c + HALO)];
+    }
+}
+
+// g of Eq. 3 in place from |grad|^2 on the tile and its ring.
+template <bool G1>
+__device__ __forceinline__ void g_from_m2(float* G, float inv_k2)
+{
+    for (int rr = threadIdx.x >> 5; rr < GROWS; rr += NWARP)
+        for (int cc = threadIdx.x & 31; cc < GCOLS; cc += 32) {
+            float* q = G + rr * GS + cc;
+            const float m2 = *q;
+            *q = G1 ? expf(-(m2 * inv_k2)) : __fdividef(1.f, fmaf(m2, inv_k2, 1.f));
+        }
 }
 
 __device__ __forceinline__ Rec load_rec(const float* s, int st)
@@ -558,15 +721,24 @@ __global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params
         s_abort = 0;
         mbar_init(&s_bar);
     }
-    const float kk = *p.d_k;
-    const float inv_k2 = 1.f / (kk * kk);
+    __shared__ float s_k;
+    __shared__ unsigned s_max;
     // lines: threads 0..TH-1 own the tile's rows, threads 128..128+TW-1 its columns
     const bool row_line = tid < th;
     const bool col_line = tid >= 128 && tid - 128 < tw;
     const int li = row_line ? tid : tid - 128;
 
-    load_all(LH, p.levels, p, x0, y0);
+    if (p.img)
+        presmooth_tile(sm, p, x0, y0, tw, th, p.levels);
+    else
+        load_all(LH, p.levels, p, x0, y0);
+    if (tid == 0) s_max = 0u;
     __syncthreads();
+    float inv_k2 = 0.f;
+    if (!p.hist) {
+        const float kk = *p.d_k;
+        inv_k2 = 1.f / (kk * kk);
+    }
 
     for (int lev = 1; lev < p.n_levels; ++lev) {
         const float tau = p.tau[lev];
@@ -578,10 +750,80 @@ __global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params
         __syncthreads();
         v_pass(G, SC, p);
         __syncthreads();
-        if (p.diffusivity == KAZE_G1)
-            scharr_pass<true>(SC, G, inv_k2);
-        else
-            scharr_pass<false>(SC, G, inv_k2);
+        if (lev == 1 && p.hist) {
+            // the contrast factor: |grad|^2 of L_0 into G, the maximum of |grad|
+            // over the interior, the histogram, the percentile; then g from
+            // |grad|^2 in place
+            float mx = scharr_pass<MODE_M2>(SC, G, 0.f, x0, y0, tw, th, p.w, p.h);
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            // non-negative floats order like their bit patterns
+            if (lane == 0 && mx > 0.f) atomicMax(&s_max, __float_as_uint(mx));
+            __syncthreads();
+            if (tid == 0 && s_max) atomicMax(p.hmax_bits, s_max);
+            nbar += ntiles;
+            if (!grid_barrier(p, nbar, &s_abort)) return;
+            const float hmax = __uint_as_float(ld_relaxed(reinterpret_cast<const int*>(p.hmax_bits)));
+            // the tile's interior image pixels binned into one histogram per
+            // warp (in SC, free after the smoothing), each thread counting a
+            // run of up to 32 consecutive pixels of a row and adding a count
+            // when the bin changes
+            unsigned* wh = reinterpret_cast<unsigned*>(SC) + warp * p.nbins;
+            for (int b = lane; b < p.nbins; b += 32) wh[b] = 0u;
+            __syncthreads();
+            const float hmax_scale = (float)p.nbins / hmax;
+            const int ylo = max(1, y0), yhi = min(p.h - 2, y0 + th - 1), xlo = max(1, x0), xhi = min(p.w - 2, x0 + tw - 1);
+            {
+                const int yy = ylo + (tid >> 2), xs = xlo + 32 * (tid & 3), xe = min(xs + 32, xhi + 1);
+                if (yy <= yhi) {
+                    const float* grow = G + (yy - y0 + 1) * GS + (1 - x0);
+                    int cur = -1;
+                    unsigned cnt = 0;
+                    for (int xx = xs; xx < xe; ++xx) {
+                        const float m = sqrtf(grow[xx]);
+                        if (!(m > 0.f)) continue;
+                        const int b = min((int)floorf(m * hmax_scale), p.nbins - 1);
+                        if (b != cur) {
+                            if (cnt) atomicAdd(&wh[cur], cnt);
+                            cur = b;
+                            cnt = 0;
+                        }
+                        ++cnt;
+                    }
+                    if (cnt) atomicAdd(&wh[cur], cnt);
+                }
+            }
+            __syncthreads();
+            for (int b = tid; b < p.nbins; b += NT) {
+                unsigned c = 0;
+                const unsigned* wb = reinterpret_cast<const unsigned*>(SC) + b;
+#pragma unroll 4
+                for (int q = 0; q < NWARP; ++q) c += wb[q * p.nbins];
+                if (c) atomicAdd(&p.hist[b], c);
+            }
+            nbar += ntiles;
+            if (!grid_barrier(p, nbar, &s_abort)) return;
+            // the whole histogram into shared memory, then the percentile
+            unsigned* hs = reinterpret_cast<unsigned*>(XE);
+            for (int b = tid; b < p.nbins; b += NT) hs[b] = __ldcg(p.hist + b);
+            __syncthreads();
+            if (warp == 0) {
+                const float kk = percentile_k(hs, p.nbins, hmax, p.pct, lane);
+                if (lane == 0) {
+                    s_k = kk;
+                    if (blockIdx.x == 0) *p.d_k = kk;
+                }
+            }
+            __syncthreads();
+            inv_k2 = 1.f / (s_k * s_k);
+            if (p.diffusivity == KAZE_G1)
+                g_from_m2<true>(G, inv_k2);
+            else
+                g_from_m2<false>(G, inv_k2);
+        } else if (p.diffusivity == KAZE_G1) {
+            scharr_pass<MODE_G1>(SC, G, inv_k2, x0, y0, tw, th, p.w, p.h);
+        } else {
+            scharr_pass<MODE_G2>(SC, G, inv_k2, x0, y0, tw, th, p.w, p.h);
+        }
         __syncthreads();
         ghost_conductance(G, x0, y0, p.w, p.h);
         __syncthreads();
@@ -734,6 +976,8 @@ cudaError_t configure_evolve_kernel()
     return cudaFuncSetAttribute(ev::k_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ev::SMEM_BYTES);
 }
 
+bool evolve_front_fits(int r0, int nbins) { return r0 == ev::R0MAX && nbins * ev::NWARP <= ev::A_SIZE; }
+
 size_t evolve_exchange_floats(int max_tiles)
 {
     // segment records of every line of every tile (rows, then columns from a
@@ -757,9 +1001,9 @@ bool evolve_fits(int w, int h, int radius, int* tiles)
 }
 
 cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int h, int n_levels, const double* t,
-                          const float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
-                          unsigned int* barrier, int* status, cudaStream_t st, long long wait_limit,
-                          int stall_tile)
+                          float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
+                          unsigned int* barrier, int* status, cudaStream_t st, const EvolveFront* front,
+                          long long wait_limit, int stall_tile)
 {
     int tiles = 0;
     if (!evolve_fits(w, h, taps.r, &tiles) || tiles > max_tiles || n_levels > kMaxLevels) return cudaErrorInvalidValue;
@@ -780,6 +1024,28 @@ cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int 
     p.xcol = exchange + (((size_t)h * p.tiles_x * ev::REC + 3) & ~(size_t)3);
     p.barrier = barrier;
     p.status = status;
+    p.img = nullptr;
+    p.img_pitch = 0;
+    p.r0 = 0;
+    for (int j = 0; j <= 2 * ev::R0MAX; ++j) p.pw[j] = 0.f;
+    p.hmax_bits = nullptr;
+    p.hist = nullptr;
+    p.nbins = 0;
+    p.pct = 0.0;
+    if (front && front->img) {
+        if (front->taps0->r != ev::R0MAX) return cudaErrorInvalidValue;
+        p.img = front->img;
+        p.img_pitch = front->img_pitch;
+        p.r0 = front->taps0->r;
+        for (int j = 0; j <= 2 * p.r0; ++j) p.pw[j] = front->taps0->w[j];
+        if (front->hist) {
+            if (front->nbins < 1 || front->nbins * ev::NWARP > ev::A_SIZE) return cudaErrorInvalidValue;
+            p.hmax_bits = front->hmax_bits;
+            p.hist = front->hist;
+            p.nbins = front->nbins;
+            p.pct = front->pct;
+        }
+    }
     p.wait_limit = wait_limit > 0 ? wait_limit : (1ll << 31);
     p.stall_tile = stall_tile;
     cudaError_t e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), st);

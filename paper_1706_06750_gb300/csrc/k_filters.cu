@@ -372,44 +372,12 @@ k_gradient4(const float* __restrict__ L, float* __restrict__ g, float* __restric
     }
 }
 
-// Percentile pick on one warp: lane l owns a contiguous slice of bins, the
-// slice sums are prefix-summed with shuffles, and the lane whose slice
-// crosses pct * n walks its bins.  k = hmax * (b + 1) / nbins; 0.03 when no
-// pixel was binned.
+// Percentile pick of the contrast factor on one warp (percentile_k), k to d_k.
 __device__ __forceinline__ void percentile_pick(const unsigned int* hist, int nbins,
                                                 const unsigned int* d_hmax_bits, double pct, float* d_k, int lane)
 {
-    const int per = (nbins + 31) / 32;
-    const int b0 = min(lane * per, nbins), b1 = min(b0 + per, nbins);
-    unsigned long long s = 0;
-    for (int b = b0; b < b1; ++b) s += hist[b];
-    unsigned long long inc = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    const unsigned long long n = __shfl_sync(0xffffffffu, inc, 31);
-    const float hmax = __uint_as_float(*d_hmax_bits);
-    if (n == 0 || !(hmax > 0.f)) {
-        if (lane == 0) *d_k = 0.03f;
-        return;
-    }
-    const double target = pct * (double)n;
-    const unsigned ballot = __ballot_sync(0xffffffffu, (double)inc >= target);
-    if (ballot == 0u) {
-        if (lane == 0) *d_k = 0.03f;
-        return;
-    }
-    if (lane == __ffs(ballot) - 1) {
-        unsigned long long cum = inc - s;
-        for (int b = b0; b < b1; ++b) {
-            cum += hist[b];
-            if ((double)cum >= target) {
-                *d_k = hmax * (float)(b + 1) / (float)nbins;
-                break;
-            }
-        }
-    }
+    const float k = percentile_k(hist, nbins, __uint_as_float(*d_hmax_bits), pct, lane);
+    if (lane == 0) *d_k = k;
 }
 
 __global__ void k_percentile(const unsigned int* __restrict__ hist, int nbins,

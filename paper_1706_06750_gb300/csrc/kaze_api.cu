@@ -26,11 +26,12 @@ namespace {
 enum KernelKind {
     KK_PRESMOOTH = 0, KK_GRAD_MAX, KK_GRAD_HIST, KK_PERCENTILE, KK_SET_SCALAR,
     KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_SURROGATE, KK_DESCRIBE, KK_FED, KK_EVOLVE,
-    KK_COUNT
+    KK_FRONT_EVOLVE, KK_COUNT
 };
 const char* const kKindNames[KK_COUNT] = {
     "presmooth", "grad_max", "grad_hist", "percentile", "set_scalar",
-    "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate", "describe", "fed", "aos_evolve"};
+    "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate", "describe", "fed", "aos_evolve",
+    "front_evolve"};
 }  // namespace
 
 struct kaze_handle {
@@ -66,11 +67,14 @@ struct kaze_handle {
     float* d_desc = nullptr;         // their descriptors, max_keypoints x 64
     unsigned int* h_count = nullptr;  // pinned
     int* h_status = nullptr;          // pinned
+    kaze_keypoint* h_kp_pre = nullptr;  // pinned: the first kp_pre keypoints, copied with the count
+    int kp_pre = 0;
 
     // current image geometry
     int cur_w = 0, cur_h = 0, cur_pitch = 0;
     long long cur_plane = 0;
     bool built = false, responded = false;
+    bool pending = false;  // a kaze_detect_enqueue awaits its kaze_detect_collect
 
     // scale table (Eq. 6-7) and filter taps
     double sigma[kz::kMaxLevels];
@@ -258,6 +262,34 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
     set_geometry(h, w, hh);
     const int P = h->cur_pitch;
     KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
+    const bool resident = h->N > 1 && !h->surrogate && h->opt.scheme == KAZE_SCHEME_AOS &&
+                          h->opt.aos_solver == KAZE_AOS_AUTO && h->d_exchange &&
+                          kz::evolve_fits(w, hh, h->tapsd.r, nullptr);
+    if (resident && kz::evolve_front_fits(h->taps0.r, h->opt.nbins)) {
+        // presmoothing, the contrast factor and every AOS step in one
+        // cooperative launch, the tiles resident in shared memory
+        kz::EvolveFront f;
+        f.img = d_img;
+        f.img_pitch = pitch_elems;
+        f.taps0 = &h->taps0;
+        if (h->opt.k_override > 0.f) {
+            KZ_LAUNCH(h, KK_SET_SCALAR, kz::launch_set_scalar(h->d_k, h->opt.k_override, st));
+        } else {
+            KZ_TRY(h, cudaMemsetAsync(h->d_hmax, 0, sizeof(unsigned int), st));
+            KZ_TRY(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned int) * h->opt.nbins, st));
+            f.hmax_bits = h->d_hmax;
+            f.hist = h->d_hist;
+            f.nbins = h->opt.nbins;
+            f.pct = h->opt.k_percentile;
+        }
+        KZ_LAUNCH(h, KK_FRONT_EVOLVE,
+                  kz::launch_evolve(h->levels, h->cur_plane, P, w, hh, h->N, h->t, h->d_k, h->tapsd,
+                                    h->opt.diffusivity, h->d_exchange, h->max_tiles, h->d_barrier, h->d_status, st,
+                                    &f, h->evolve_wait_limit, h->evolve_stall_tile));
+        h->built = true;
+        h->responded = false;
+        return KAZE_OK;
+    }
     KZ_LAUNCH(h, KK_PRESMOOTH, kz::launch_gaussian(d_img, pitch_elems, level_ptr(h, 0), P, w, hh, h->taps0, st));
     // with k measured here, |grad(G * L_0)|^2 stays in the conductance plane
     // and the first conductance is computed from it
@@ -271,14 +303,12 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
                       kz::launch_conductance(Lp, h->g, zero, P, w, hh, h->tapsd, h->d_k, h->opt.diffusivity, st));
         return KAZE_OK;
     };
-    if (h->N > 1 && !h->surrogate && h->opt.scheme == KAZE_SCHEME_AOS && h->opt.aos_solver == KAZE_AOS_AUTO &&
-        h->d_exchange && kz::evolve_fits(w, hh, h->tapsd.r, nullptr)) {
-        // every AOS step in one cooperative launch, the tiles resident in
-        // shared memory
+    if (resident) {
+        // every AOS step in one cooperative launch from level 0 in its plane
         KZ_LAUNCH(h, KK_EVOLVE,
                   kz::launch_evolve(h->levels, h->cur_plane, P, w, hh, h->N, h->t, h->d_k, h->tapsd,
                                     h->opt.diffusivity, h->d_exchange, h->max_tiles, h->d_barrier, h->d_status, st,
-                                    h->evolve_wait_limit, h->evolve_stall_tile));
+                                    nullptr, h->evolve_wait_limit, h->evolve_stall_tile));
         h->built = true;
         h->responded = false;
         return KAZE_OK;
@@ -359,10 +389,15 @@ kaze_status enqueue_extrema(kaze_handle* h, const float* D, int pitch, long long
                                  h->opt.max_keypoints, h->d_count, h->stream));
     KZ_TRY(h, cudaMemcpyAsync(h->h_count, h->d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
     KZ_TRY(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    // the first kp_pre keypoint slots go with the count, so that a detection
+    // with no more keypoints than that needs no second round trip to the host
+    KZ_TRY(h, cudaMemcpyAsync(h->h_kp_pre, h->d_kp, sizeof(kaze_keypoint) * h->kp_pre, cudaMemcpyDeviceToHost,
+                              h->stream));
     return KAZE_OK;
 }
 
-// After enqueue_extrema: wait, copy the keypoints, sort by (level, iy, ix).
+// After enqueue_extrema: wait, take the keypoints (from the slots copied with
+// the count, or by a second copy when there are more), sort by (level, iy, ix).
 kaze_status collect_keypoints(kaze_handle* h, kaze_keypoint* out, int capacity, int* count)
 {
     KZ_TRY(h, cudaStreamSynchronize(h->stream));
@@ -370,7 +405,9 @@ kaze_status collect_keypoints(kaze_handle* h, kaze_keypoint* out, int capacity, 
     const unsigned total = *h->h_count;
     const unsigned have = std::min<unsigned>(total, (unsigned)h->opt.max_keypoints);
     h->hkp.resize(have);
-    if (have) {
+    if (have && have <= (unsigned)h->kp_pre) {
+        std::memcpy(h->hkp.data(), h->h_kp_pre, sizeof(kaze_keypoint) * have);
+    } else if (have) {
         KZ_TRY(h, cudaMemcpyAsync(h->hkp.data(), h->d_kp, sizeof(kaze_keypoint) * have, cudaMemcpyDeviceToHost,
                                   h->stream));
         KZ_TRY(h, cudaStreamSynchronize(h->stream));
@@ -659,6 +696,14 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     *h->h_count = 0;
     h->h_status = (int*)(h->h_count + 1);
     *h->h_status = 0;
+    h->kp_pre = std::min(o.max_keypoints, kz::kKeypointsWithCount);
+    e = cudaMallocHost(&h->h_kp_pre, sizeof(kaze_keypoint) * h->kp_pre);
+    if (e != cudaSuccess) {
+        cudaFreeHost(h->h_count);
+        cudaFree(h->arena);
+        delete h;
+        return create_fail(KAZE_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorName(e));
+    }
     if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
@@ -761,6 +806,24 @@ KAZE_API kaze_status kaze_detect(kaze_handle* h, const float* d_img, int w, int 
     KZ_CHECK(check_image(h, w, hh));
     if (pitch_elems < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
     KZ_CHECK(run_detect_graph(h, d_img, w, hh, pitch_elems));
+    return collect_keypoints(h, h_out, capacity, count);
+}
+
+KAZE_API kaze_status kaze_detect_enqueue(kaze_handle* h, const float* d_img, int w, int hh, int pitch_elems)
+{
+    if (!h || !d_img) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    KZ_CHECK(check_image(h, w, hh));
+    if (pitch_elems < w) return fail(h, KAZE_ERR_INVALID_ARG, "pitch smaller than width");
+    KZ_CHECK(run_detect_graph(h, d_img, w, hh, pitch_elems));
+    h->pending = true;
+    return KAZE_OK;
+}
+
+KAZE_API kaze_status kaze_detect_collect(kaze_handle* h, kaze_keypoint* h_out, int capacity, int* count)
+{
+    if (!h || capacity < 0 || (capacity > 0 && !h_out)) return fail(h, KAZE_ERR_INVALID_ARG, "null argument");
+    if (!h->pending) return fail(h, KAZE_ERR_STATE, "no detection enqueued");
+    h->pending = false;
     return collect_keypoints(h, h_out, capacity, count);
 }
 
@@ -1236,6 +1299,7 @@ KAZE_API void kaze_destroy(kaze_handle* h)
     drop_graph(h);
     if (h->arena) cudaFree(h->arena);
     if (h->h_count) cudaFreeHost(h->h_count);
+    if (h->h_kp_pre) cudaFreeHost(h->h_kp_pre);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_copied) cudaEventDestroy(h->ev_copied);

@@ -16,6 +16,7 @@ constexpr int kMaxGaussR = 16;     // presmoothing radius bound (sigma <= 5.33)
 constexpr int kMaxGradR = 6;       // gradient-smoothing radius bound (sigma_d <= 2)
 constexpr int kMaxBins = 4096;
 constexpr int kMaxDynSmem = 227 * 1024;  // opt-in dynamic shared memory per CTA
+constexpr int kKeypointsWithCount = 4096;  // keypoint slots copied to the host with the count
 
 // Sampled, normalised Gaussian taps w[0..2r] for offsets -r..r.
 struct GaussTaps {
@@ -79,6 +80,43 @@ __device__ __forceinline__ float doh_value(const float* hd, const float* hs, con
     const float lyy = fmaf(-2.f, hs[2], hs[0] + hs[4]);
     const float lxy = fmaf(10.f, hx[3] - hx[1], 3.f * (hx[4] - hx[0]));
     return scale * fmaf(lxx, lyy, -(lxy * lxy));
+}
+
+// Contrast factor k from the histogram of gradient magnitudes (Sec. III-1,
+// reading R4), on one full warp: lane l owns a contiguous slice of bins, the
+// slice sums are prefix-summed with shuffles, and the lane whose slice
+// crosses pct * n walks its bins; k = hmax (b + 1) / nbins for the first bin
+// b where the cumulative count reaches pct * n, 0.03 when nothing was binned.
+// Returns k to every lane.
+__device__ __forceinline__ float percentile_k(const unsigned int* hist, int nbins, float hmax, double pct, int lane)
+{
+    const int per = (nbins + 31) / 32;
+    const int b0 = min(lane * per, nbins), b1 = min(b0 + per, nbins);
+    unsigned long long s = 0;
+    for (int b = b0; b < b1; ++b) s += hist[b];
+    unsigned long long inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const unsigned long long n = __shfl_sync(0xffffffffu, inc, 31);
+    if (n == 0 || !(hmax > 0.f)) return 0.03f;
+    const double target = pct * (double)n;
+    const unsigned ballot = __ballot_sync(0xffffffffu, (double)inc >= target);
+    if (ballot == 0u) return 0.03f;
+    const int src = __ffs(ballot) - 1;
+    float k = 0.03f;
+    if (lane == src) {
+        unsigned long long cum = inc - s;
+        for (int b = b0; b < b1; ++b) {
+            cum += hist[b];
+            if ((double)cum >= target) {
+                k = hmax * (float)(b + 1) / (float)nbins;
+                break;
+            }
+        }
+    }
+    return __shfl_sync(0xffffffffu, k, src);
 }
 
 // Raises a kernel's dynamic shared-memory limit to what the device allows
@@ -160,13 +198,29 @@ size_t aos_cols_smem_bytes(int h);
 // one counter; a timed-out grid barrier sets bit 0 of *status.  wait_limit:
 // SM cycles a barrier wait may take (0: 2^31); stall_tile >= 0 (a test
 // hook) makes that tile never arrive, so every wait runs out.
+// The front of the pipeline inside the same launch: with `img`, level 0 is
+// the presmoothing of the image (radius taps0->r == 5, sigma0 in (4/3, 5/3])
+// instead of being read;
+// with `hist` too (nbins counters and hmax_bits zeroed beforehand, nbins <=
+// 1030), the contrast factor is measured inside (maximum and histogram of
+// step 1's gradient magnitudes, the percentile pct) and written to d_k.
+struct EvolveFront {
+    const float* img = nullptr;
+    int img_pitch = 0;
+    const GaussTaps* taps0 = nullptr;
+    unsigned int* hmax_bits = nullptr;
+    unsigned int* hist = nullptr;
+    int nbins = 0;
+    double pct = 0.0;
+};
 cudaError_t configure_evolve_kernel();
 size_t evolve_exchange_floats(int max_tiles);
 bool evolve_fits(int w, int h, int radius, int* tiles);
+bool evolve_front_fits(int r0, int nbins);
 cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int h, int n_levels, const double* t,
-                          const float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
-                          unsigned int* barrier, int* status, cudaStream_t st, long long wait_limit = 0,
-                          int stall_tile = -1);
+                          float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
+                          unsigned int* barrier, int* status, cudaStream_t st, const EvolveFront* front = nullptr,
+                          long long wait_limit = 0, int stall_tile = -1);
 
 // Detector response of Eq. 8 for levels [l0, l0 + nl) of a level stack.
 // Number of kernels launch_doh issues for levels l0 .. l0 + nl - 1.

@@ -98,6 +98,8 @@ _SIGNATURES = {
     "kaze_build_scale_space": (_i, [_vp, _vp, _i, _i, _i]),
     "kaze_get_level": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_f)]),
     "kaze_get_level_scale": (_i, [_vp, _i, ctypes.POINTER(_f), ctypes.POINTER(_f)]),
+    "kaze_detect_enqueue": (_i, [_vp, _vp, _i, _i, _i]),
+    "kaze_detect_collect": (_i, [_vp, ctypes.POINTER(Keypoint), _i, ctypes.POINTER(_i)]),
     "kaze_set_evolve_wait_limit": (_i, [_vp, ctypes.c_longlong, _i]),
     "kaze_get_contrast": (_i, [_vp, ctypes.POINTER(_f)]),
     "kaze_detector_response": (_i, [_vp]),
@@ -399,6 +401,26 @@ class Kaze:
                                           ctypes.byref(n)), "kaze_detect")
         self._end()
         self._w, self._hh = w, h
+        self.last_status = st
+        self.last_count = n.value
+        return _sorted_keypoints(buf, min(n.value, cap))
+
+    def detect_enqueue(self, img):
+        """The first half of detect: replay the detection without waiting."""
+        w, h, pitch = _check_image(img)
+        self._begin()
+        self._ck(self._L.kaze_detect_enqueue(self._h, _vp(img.data_ptr()), w, h, pitch), "kaze_detect_enqueue")
+        self._w, self._hh = w, h
+
+    def detect_collect(self, capacity=None):
+        """The second half of detect: wait for the enqueued detection and
+        return its keypoints."""
+        cap = self.options.max_keypoints if capacity is None else int(capacity)
+        buf = self._kp_buf if cap <= len(self._kp_buf) else (Keypoint * cap)()
+        n = _i()
+        self._begin()
+        st = self._ck(self._L.kaze_detect_collect(self._h, buf, cap, ctypes.byref(n)), "kaze_detect_collect")
+        self._end()
         self.last_status = st
         self.last_count = n.value
         return _sorted_keypoints(buf, min(n.value, cap))

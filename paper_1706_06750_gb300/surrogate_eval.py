@@ -11,11 +11,11 @@ method) and once with the surrogate standing in for every AOS step.  Reported:
 * keypoint repeatability: the share of AOS keypoints that the surrogate's
   detection reproduces on the same level within 1 and 2.5 pixels, and the
   share of surrogate keypoints that AOS confirms within 2.5 pixels;
-* time: the evolution kernels of one detection, conductance included (the
-  resident AOS evolution computes it inside its one launch; the surrogate
-  path launches it per level), with CUDA events from ``kaze_profile``, and a
-  batched step of all images in one fused launch against one AOS step per
-  image.
+* time: the scale space of one detection (presmoothing, contrast factor,
+  conductances and the evolution; the resident AOS evolution takes them in
+  one launch, the surrogate path in separate ones), with CUDA events from
+  ``kaze_profile``, and a batched step of all images in one fused launch
+  against one AOS step per image.
 
 Only the library is used; the FP64 oracle plays no part here.
 """
@@ -100,8 +100,9 @@ def evaluate(surrogate, images, octaves=4, sublevels=4, batch_reps=5):
         n_sg.append(len(kp_s))
         pa = aos.profile(img)
         ps = sgk.profile(img)
-        t_aos.append(sum(pa[kind][0] for kind in ("aos_evolve", "conductance", "aos_rows", "aos_cols")))
-        t_sg.append(ps["surrogate"][0] + ps["conductance"][0])
+        # the scale space of one detection: everything but the response and extrema
+        t_aos.append(sum(ms for kind, (ms, n) in pa.items() if kind not in ("doh", "extrema")))
+        t_sg.append(sum(ms for kind, (ms, n) in ps.items() if kind not in ("doh", "extrema")))
 
     # batched step: every image's first step (L_0 and its conductance) in
     # one fused launch, against one AOS step per image (kaze_op_aos_step)

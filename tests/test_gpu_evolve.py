@@ -59,8 +59,10 @@ def test_resident_scale_space_against_oracle(kz, shape):
         np.random.default_rng(h * 1000 + w).random(shape).astype(np.float32)
     k = k_of(img)
     lv_g, prof = gpu_levels(kz, img, 2, 4, k)
-    assert prof["aos_evolve"][1] == 1, prof
-    assert prof["aos_rows"][1] == 0 and prof["aos_cols"][1] == 0 and prof["conductance"][1] == 0
+    # presmoothing, the contrast factor and every step in one launch
+    assert prof["front_evolve"][1] == 1, prof
+    for kind in ("presmooth", "grad_max", "grad_hist", "aos_rows", "aos_cols", "conductance", "aos_evolve"):
+        assert prof[kind][1] == 0, (kind, prof)
     lv_r = oracle_levels(img, 2, 4, k)
     err = np.max(np.abs(lv_g - lv_r), axis=(1, 2))
     assert np.all(err <= SCALE_TOL), err
@@ -70,7 +72,7 @@ def test_resident_g1_against_oracle(kz):
     img = synth.image(250, 190, 77)
     k = k_of(img)
     lv_g, prof = gpu_levels(kz, img, 2, 4, k, diffusivity=kz.G1)
-    assert prof["aos_evolve"][1] == 1
+    assert prof["front_evolve"][1] == 1
     lv_r = oracle_levels(img, 2, 4, k, diffusivity=oracle.G1)
     assert np.max(np.abs(lv_g - lv_r)) <= SCALE_TOL
 
@@ -81,9 +83,9 @@ def test_resident_and_line_kernels_at_1920x1200(kz):
     img = synth.workload_image("1920x1200")
     k = k_of(img)
     lv_a, prof = gpu_levels(kz, img, 4, 4, k)
-    assert prof["aos_evolve"][1] == 1
+    assert prof["front_evolve"][1] == 1
     lv_l, prof_l = gpu_levels(kz, img, 4, 4, k, aos_solver=kz.AOS_LINES)
-    assert prof_l["aos_evolve"][1] == 0 and prof_l["aos_rows"][1] == 15
+    assert prof_l["front_evolve"][1] == 0 and prof_l["aos_rows"][1] == 15
     lv_r = oracle_levels(img, 4, 4, k)
     ea = np.max(np.abs(lv_a - lv_r), axis=(1, 2))
     el = np.max(np.abs(lv_l - lv_r), axis=(1, 2))
@@ -98,7 +100,7 @@ def test_resident_too_large_falls_back_to_lines(kz):
     # 32 x 26 tiles do not fit one per SM: the line kernels run
     with kz.Kaze(4096, 3072, octaves=1, sublevels=2) as kh:
         prof = kh.profile(torch.rand(3072, 4096, device="cuda"))
-    assert prof["aos_evolve"][1] == 0 and prof["aos_rows"][1] == 1
+    assert prof["front_evolve"][1] == 0 and prof["aos_rows"][1] == 1
 
 
 def test_stalled_barrier_times_out_and_the_handle_recovers(kz):
@@ -113,3 +115,26 @@ def test_stalled_barrier_times_out_and_the_handle_recovers(kz):
         kh.set_evolve_wait_limit(0, -1)
         again = kh.detect(x)
     assert np.array_equal(ref, again)
+
+
+@pytest.mark.parametrize("shape", [(1200, 1920), (131, 257), (7, 300)])
+def test_resident_front_matches_the_separate_kernels(kz, shape):
+    """With the presmoothing and the contrast factor inside the resident
+    launch, L_0 and the histogram's percentile are those of the presmoothing
+    and contrast kernels (the same operations in the same order): L_0 and k
+    are equal bit for bit, and every later level within FP32 rounding of the
+    line kernels' (which start from the same L_0 and k)."""
+    h, w = shape
+    img = synth.image(w, h, 21 + h) if min(shape) >= 16 else \
+        np.random.default_rng(3).random(shape).astype(np.float32)
+    x = dev(img)
+    with kz.Kaze(w, h, octaves=2, sublevels=4) as a, kz.Kaze(w, h, octaves=2, sublevels=4,
+                                                           aos_solver=kz.AOS_LINES) as b:
+        a.build_scale_space(x)
+        b.build_scale_space(x)
+        assert a.contrast() == b.contrast()
+        la, lb = a.levels(), b.levels()
+        assert torch.equal(la[0], lb[0])
+        assert (la - lb).abs().max().item() <= 2 * SCALE_TOL
+        pa = a.profile(x)
+    assert pa["front_evolve"][1] == 1 and pa["presmooth"][1] == 0 and pa["grad_max"][1] == 0
