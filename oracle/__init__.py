@@ -101,8 +101,14 @@ def build(force: bool = False) -> str:
             return _LIB_PATH
         os.makedirs(_BUILD_DIR, exist_ok=True)
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        # loops over independent pixels and lines on every host core where
+        # gcc offers OpenMP (the same results with any thread count)
+        try:
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                                   "-o", tmp, _SRC, "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                                   "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
 
@@ -118,6 +124,8 @@ def _load():
     d = ctypes.c_double
     sig = {
         "ko_reflect": (ctypes.c_long, [ctypes.c_long, ctypes.c_long]),
+        "ko_set_threads": (None, [i]),
+        "ko_threads": (i, []),
         "ko_scale_table": (None, [i, i, d, dp, dp]),
         "ko_gaussian_weights": (i, [d, dp, i]),
         "ko_gaussian": (None, [dp, dp, i, i, d]),
@@ -160,6 +168,16 @@ def _out(shape):
 
 def reflect(i: int, n: int) -> int:
     return int(_load().ko_reflect(i, n))
+
+
+def set_threads(n: int) -> None:
+    """Host threads for the oracle's loops over independent pixels and lines
+    (the results do not depend on it)."""
+    _load().ko_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(_load().ko_threads())
 
 
 def scale_table(octaves: int, sublevels: int, sigma0: float = 1.6):

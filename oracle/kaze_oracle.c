@@ -4,7 +4,11 @@
  * TEST INFRASTRUCTURE ONLY: used by the test suite, the smoke check and the
  * CPU-baseline leg of the benchmark; never by the product path.  Written for
  * readability, not speed: one function per step of the method, in the order
- * the paper describes them, with no fusion or blocking.
+ * the paper describes them, with no fusion or blocking.  Loops over
+ * independent pixels or lines may run on several host threads (OpenMP, when
+ * the compiler offers it; ko_set_threads): each output is computed by the
+ * same operations either way, so the results do not depend on the thread
+ * count.
  *
  * Readings of passages where the paper is silent or garbled (each also listed
  * in the design notes):
@@ -35,6 +39,28 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads for the loops over independent pixels and lines (1: serial). */
+void ko_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int ko_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* R1: index i reflected into [0, n) by half-sample symmetric extension
  * (... 2 1 0 | 0 1 2 ... n-1 | n-1 n-2 ...), repeated for tiny n. */
@@ -84,12 +110,14 @@ void ko_gaussian(const double* in, double* out, int W, int H, double sigma)
     double w[512];
     int r = ko_gaussian_weights(sigma, w, 512);
     double* tmp = (double*)malloc(sizeof(double) * (size_t)W * H);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             double acc = 0.0;
             for (int j = -r; j <= r; ++j) acc += w[j + r] * at(in, W, H, x + j, y);
             tmp[(long)y * W + x] = acc;
         }
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             double acc = 0.0;
@@ -105,6 +133,7 @@ void ko_gaussian(const double* in, double* out, int W, int H, double sigma)
 void ko_scharr(const double* L, double* Lx, double* Ly, int W, int H)
 {
     const double c[3] = {3.0 / 16.0, 10.0 / 16.0, 3.0 / 16.0};
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             double gx = 0.0, gy = 0.0;
@@ -181,6 +210,7 @@ void ko_conductance(const double* L, int W, int H, double sigma_d, double k,
     double* Ly = (double*)malloc(sizeof(double) * P);
     ko_gaussian(L, Ls, W, H, sigma_d);
     ko_scharr(Ls, Lx, Ly, W, H);
+#pragma omp parallel for schedule(static)
     for (size_t p = 0; p < P; ++p) {
         double q = (Lx[p] * Lx[p] + Ly[p] * Ly[p]) / (k * k);
         g[p] = diffusivity == KO_G1 ? exp(-q) : 1.0 / (1.0 + q);
@@ -236,32 +266,39 @@ void ko_aos_step(const double* Lprev, const double* g, int W, int H,
     int n = W > H ? W : H;
     double* vx = (double*)malloc(sizeof(double) * P);
     double* vy = (double*)malloc(sizeof(double) * P);
-    double* gl = (double*)malloc(sizeof(double) * (size_t)n);
-    double* dl = (double*)malloc(sizeof(double) * (size_t)n);
-    double* vl = (double*)malloc(sizeof(double) * (size_t)n);
 
-    for (int y = 0; y < H; ++y) {          /* x direction: every row */
-        for (int x = 0; x < W; ++x) {
-            gl[x] = g[(size_t)y * W + x];
-            dl[x] = Lprev[(size_t)y * W + x];
+#pragma omp parallel
+    {
+        /* one line's conductance, right-hand side and solution per thread */
+        double* gl = (double*)malloc(sizeof(double) * (size_t)n);
+        double* dl = (double*)malloc(sizeof(double) * (size_t)n);
+        double* vl = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(static)
+        for (int y = 0; y < H; ++y) {          /* x direction: every row */
+            for (int x = 0; x < W; ++x) {
+                gl[x] = g[(size_t)y * W + x];
+                dl[x] = Lprev[(size_t)y * W + x];
+            }
+            aos_line(W, gl, dl, tau, vl);
+            for (int x = 0; x < W; ++x) vx[(size_t)y * W + x] = vl[x];
         }
-        aos_line(W, gl, dl, tau, vl);
-        for (int x = 0; x < W; ++x) vx[(size_t)y * W + x] = vl[x];
-    }
-    for (int x = 0; x < W; ++x) {          /* y direction: every column */
-        for (int y = 0; y < H; ++y) {
-            gl[y] = g[(size_t)y * W + x];
-            dl[y] = Lprev[(size_t)y * W + x];
+#pragma omp for schedule(static)
+        for (int x = 0; x < W; ++x) {          /* y direction: every column */
+            for (int y = 0; y < H; ++y) {
+                gl[y] = g[(size_t)y * W + x];
+                dl[y] = Lprev[(size_t)y * W + x];
+            }
+            aos_line(H, gl, dl, tau, vl);
+            for (int y = 0; y < H; ++y) vy[(size_t)y * W + x] = vl[y];
         }
-        aos_line(H, gl, dl, tau, vl);
-        for (int y = 0; y < H; ++y) vy[(size_t)y * W + x] = vl[y];
+        free(gl); free(dl); free(vl);
     }
     for (size_t p = 0; p < P; ++p) {
         if (Lnext) Lnext[p] = 0.5 * (vx[p] + vy[p]);
         if (ux) ux[p] = vx[p];
         if (uy) uy[p] = vy[p];
     }
-    free(vx); free(vy); free(gl); free(dl); free(vl);
+    free(vx); free(vy);
 }
 
 /* Stopping time of one FED cycle of n steps with limit tau_max. */
@@ -355,6 +392,7 @@ int ko_fed_order(int n, const double* tau, int* order)
 /* F4: explicit step of div(g grad L) in the flux form of the AOS operator. */
 void ko_fed_step(const double* L, const double* g, int W, int H, double tau, double* out)
 {
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             const size_t p = (size_t)y * W + x;
@@ -451,6 +489,7 @@ void ko_hessian(const double* L, int W, int H, int s,
             ss[p + q] += smo[p] * smo[q];
             ds[p + q] += dif[p] * smo[q];
         }
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             double xx = 0.0, yy = 0.0, xy = 0.0;
@@ -485,6 +524,7 @@ void ko_doh(const double* L, int W, int H, double sigma_i, int octave,
     } else {
         norm = (double)s * s * s * s;
     }
+#pragma omp parallel for schedule(static)
     for (size_t p = 0; p < P; ++p) D[p] = norm * (xx[p] * yy[p] - xy[p] * xy[p]);
     free(xx); free(yy); free(xy);
 }

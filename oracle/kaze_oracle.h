@@ -61,6 +61,11 @@ typedef struct {
 } ko_keypoint;
 
 /* Half-sample symmetric index reflection into [0, n). */
+/* Host threads for the loops over independent pixels and lines (the
+ * results do not depend on it); ko_threads: the count in use. */
+void ko_set_threads(int n);
+int ko_threads(void);
+
 long ko_reflect(long i, long n);
 
 /* Eq. 6 / Eq. 7: sigma_i = sigma0 * 2^(o + s/S), t_i = sigma_i^2 / 2, N = O*S. */

@@ -99,9 +99,11 @@ def test_fed_zero_time_copies(kz):
 
 def test_pipeline_fed_256(kz):
     """The whole detection with FED levels against the oracle's FED scale
-    space (same k on both sides): levels within 1e-4, responses within
-    1e-4 of each level's max |DoH| plus the level error propagated, and
-    the keypoints agree (>= 99 %)."""
+    space (same k on both sides), at the tolerances of the AOS pipeline:
+    levels within 2e-5, responses within 1e-4 of each level's max |DoH|,
+    keypoints >= 99.5 % (the cycle order keeps the FP32 rounding of a
+    cycle to a few ulp times its amplification bound; measured errors stay
+    below 1e-6 at 1920x1200, test_gpu_fullsize)."""
     img = synth.workload_image("256x256")
     s0 = float(np.float32(1.6))
     L0 = oracle.gaussian(img.astype(np.float64), s0)
@@ -119,12 +121,12 @@ def test_pipeline_fed_256(kz):
     steps = sum(launches_for(len(oracle.fed_tau(t[i] - t[i - 1]))) for i in range(1, 8))
     assert launches == 1 + 1 + 7 + steps + 1 + 1      # presmooth, set k, conductances, steps, doh, extrema
     err = np.max(np.abs(lv_g - lv_r), axis=(1, 2))
-    assert np.all(err <= 1e-4), err
+    assert np.all(err <= 2e-5), err
     dmax = np.max(np.abs(D_r), axis=(1, 2))
     derr = np.max(np.abs(D_g - D_r), axis=(1, 2))
-    assert np.all(derr <= 1e-3 * dmax + 1e-9), derr / dmax
+    assert np.all(derr <= 1e-4 * dmax + 1e-12), derr / dmax
     ov, m, ur, ug, md = compare(kp_r, kp_g, D_r)
-    assert len(kp_r) >= 10 and ov >= 0.99, (ov, len(kp_r), len(kp_g))
+    assert len(kp_r) >= 10 and ov >= 0.995, (ov, len(kp_r), len(kp_g))
 
 
 def test_fed_full_size_invariants(kz):

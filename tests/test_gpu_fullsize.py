@@ -1,0 +1,125 @@
+"""The whole pipeline against the FP64 oracle at the workloads' own sizes
+(needs a GB300; the oracle runs its independent loops on every host core):
+
+* the 4096x3072 image with its sinusoidal texture, 4 x 4 levels: every
+  level, every response and the keypoints (the line kernels: its 32 x 26
+  tiles exceed one a SM);
+* two members of the 64-image mixed-size batch (a 640x480 and a 1280x720
+  image) through the single persistent launch, against the oracle's
+  detection of each;
+* the FED evolution (Eq. 5) of the 1920x1200 workload image, against the
+  oracle's FED scale space.
+
+Tolerances are those of the single-image parity tests: levels within 2e-5,
+responses within 1e-4 of each level's max |DoH|, keypoints matched on the
+same level within 0.5 px for at least 99.5 % (misses explained by decisions
+within rounding of their boundary excepted, kp_match.compare).  Both sides
+use the oracle's contrast factor (the GPU's is checked to be in the same or
+the adjacent histogram bin)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1706_06750_gb300 import synth  # noqa: E402
+
+from kp_match import compare  # noqa: E402
+
+SCALE_TOL = 2e-5
+DOH_REL_TOL = 1e-4
+KP_OVERLAP = 0.995
+
+
+@pytest.fixture(scope="module")
+def kz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_06750_gb300 import build, kaze
+    build.build()
+    oracle.build()
+    import os
+    oracle.set_threads(os.cpu_count() or 1)
+    return kaze
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def oracle_k(img):
+    L0 = oracle.gaussian(img.astype(np.float64), 1.6)
+    k, hmax, _, _ = oracle.contrast_k(L0)
+    return k, hmax
+
+
+def check_levels_responses(lv_g, D_g, lv_r, D_r):
+    for i in range(lv_r.shape[0]):
+        err = np.max(np.abs(lv_g[i] - lv_r[i]))
+        assert err <= SCALE_TOL, (i, err)
+        dmax = np.max(np.abs(D_r[i]))
+        derr = np.max(np.abs(D_g[i] - D_r[i]))
+        assert derr <= DOH_REL_TOL * dmax + 1e-12, (i, derr / dmax)
+
+
+def test_pipeline_4096x3072_against_oracle(kz):
+    img = synth.workload_image("4096x3072")
+    h, w = img.shape
+    k_ref, hmax = oracle_k(img)
+    with kz.Kaze(w, h, octaves=4, sublevels=4) as k:
+        k.build_scale_space(dev(img))
+        assert abs(k.contrast() - k_ref) <= hmax / 300 * 1.0001 + 1e-7
+    kf = float(np.float32(k_ref))
+    with kz.Kaze(w, h, octaves=4, sublevels=4, k_override=kf) as k:
+        kp_g = k.detect(dev(img))
+        lv_g = k.levels().cpu().numpy().astype(np.float64)
+        D_g = k.responses().cpu().numpy().astype(np.float64)
+    opt = oracle.Options.make(octaves=4, sublevels=4, k_override=kf, dthreshold=float(np.float32(0.001)))
+    lv_r, D_r, kp_r, _ = oracle.kaze_detect(img.astype(np.float64), opt)
+    check_levels_responses(lv_g, D_g, lv_r, D_r)
+    ov, m, ur, ug, md = compare(kp_r, kp_g, D_r)
+    assert len(kp_r) >= 1000 and ov >= KP_OVERLAP, (ov, len(kp_r), len(kp_g), ur[:3], ug[:3])
+
+
+@pytest.mark.parametrize("size", [(640, 480), (1280, 720)])
+def test_batch_member_against_oracle(kz, size):
+    """The 64-image workload in one persistent launch with the member's
+    oracle k for every image; the member against the oracle."""
+    sizes = synth.batch_sizes(64)
+    j = sizes.index(size)
+    imgs = synth.batch_images(64)
+    img = imgs[j]
+    k_ref, _ = oracle_k(img)
+    kf = float(np.float32(k_ref))
+    xs = [torch.from_numpy(a).cuda() for a in imgs]
+    with kz.Batch(sizes, k_override=kf) as b:
+        b.set_tuning(kz.BATCH_PERSISTENT, 4, 2, 8)
+        assert b.tuning()[0] == kz.BATCH_PERSISTENT
+        kps = b.detect(xs)
+        lv_g = np.stack([b.level(j, l).cpu().numpy() for l in range(16)]).astype(np.float64)
+        D_g = np.stack([b.response(j, l).cpu().numpy() for l in range(16)]).astype(np.float64)
+    opt = oracle.Options.make(octaves=4, sublevels=4, k_override=kf, dthreshold=float(np.float32(0.001)))
+    lv_r, D_r, kp_r, _ = oracle.kaze_detect(img.astype(np.float64), opt)
+    check_levels_responses(lv_g, D_g, lv_r, D_r)
+    ov, m, ur, ug, md = compare(kp_r, kps[j], D_r)
+    assert len(kp_r) >= 20 and ov >= KP_OVERLAP, (ov, len(kp_r), len(kps[j]))
+
+
+def test_fed_pipeline_1920x1200_against_oracle(kz):
+    img = synth.workload_image("1920x1200")
+    k_ref, _ = oracle_k(img)
+    kf = float(np.float32(k_ref))
+    with kz.Kaze(1920, 1200, octaves=4, sublevels=4, k_override=kf, scheme=kz.SCHEME_FED) as k:
+        kp_g = k.detect(dev(img))
+        lv_g = k.levels().cpu().numpy().astype(np.float64)
+        D_g = k.responses().cpu().numpy().astype(np.float64)
+    opt = oracle.Options.make(octaves=4, sublevels=4, k_override=kf, scheme=oracle.SCHEME_FED,
+                              dthreshold=float(np.float32(0.001)))
+    lv_r, D_r, kp_r, _ = oracle.kaze_detect(img.astype(np.float64), opt)
+    err = [float(np.max(np.abs(lv_g[i] - lv_r[i]))) for i in range(16)]
+    print("FED 1920x1200 level errors:", ["%.2e" % e for e in err])
+    check_levels_responses(lv_g, D_g, lv_r, D_r)
+    ov, m, ur, ug, md = compare(kp_r, kp_g, D_r)
+    assert len(kp_r) >= 100 and ov >= KP_OVERLAP, (ov, len(kp_r), len(kp_g))

@@ -148,3 +148,21 @@ def test_scale_space_invariants(oracle_mod):
     lv, k = oracle_mod.build_scale_space(np.full((9, 11), 0.25), opt)
     assert np.max(np.abs(lv - 0.25)) < 1e-14
     assert k == 0.03
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count(oracle_mod):
+    """The loops over independent pixels and lines may run on several host
+    threads; every output is computed by the same operations either way."""
+    from paper_1706_06750_gb300 import synth
+    img = synth.image(97, 61, 77).astype(np.float64)
+    opt = oracle_mod.Options.make(octaves=2, sublevels=4)
+    n0 = oracle_mod.threads()
+    try:
+        oracle_mod.set_threads(1)
+        lv1, D1, kp1, k1 = oracle_mod.kaze_detect(img, opt)
+        oracle_mod.set_threads(max(4, n0))
+        lv4, D4, kp4, k4 = oracle_mod.kaze_detect(img, opt)
+    finally:
+        oracle_mod.set_threads(n0)
+    assert k1 == k4 and np.array_equal(lv1, lv4) and np.array_equal(D1, D4)
+    assert np.array_equal(kp1, kp4)
