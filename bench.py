@@ -223,15 +223,32 @@ def ncu_traffic(kind):
 
 # ------------------------------------------------------------------ oracle --
 
-def oracle_sample_rate(img, seconds_budget, octaves=OCTAVES, sublevels=SUBLEVELS):
-    """Times the FP64 oracle (single thread) on a centred crop sized to the
-    budget; returns (Mpixel/s, crop w, crop h, seconds)."""
+def oracle_full_rate(img, threads, octaves=OCTAVES, sublevels=SUBLEVELS):
+    """Times the FP64 oracle on the whole image with `threads` host threads
+    (its loops over independent pixels and lines); returns (Mpixel/s,
+    seconds)."""
     import numpy as np
 
     import oracle
     oracle.build()
+    oracle.set_threads(threads)
+    opt = oracle.Options.make(octaves=octaves, sublevels=sublevels)
+    t0 = time.perf_counter()
+    oracle.kaze_detect(np.ascontiguousarray(img, dtype=np.float64), opt)
+    dt = time.perf_counter() - t0
+    return img.size / dt / 1e6, dt
+
+
+def oracle_sample_rate(img, seconds_budget, octaves=OCTAVES, sublevels=SUBLEVELS, threads=1):
+    """Times the FP64 oracle with `threads` host threads on a centred crop
+    sized to the budget; returns (Mpixel/s, crop w, crop h, seconds)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    oracle.set_threads(threads)
     h, w = img.shape
-    sec_per_px = 9e-6  # rough FP64 oracle cost per pixel for 16 levels
+    sec_per_px = 9e-6 / max(1, threads)  # rough FP64 oracle cost per pixel for 16 levels
     area = max(64 * 64, min(w * h, int(seconds_budget / sec_per_px)))
     scale = min(1.0, (area / (w * h)) ** 0.5)
     cw, ch = max(32, int(w * scale)), max(32, int(h * scale))
@@ -318,24 +335,26 @@ def run_reference(args, rank, world):
         return 0
     from paper_1706_06750_gb300 import synth
     img = synth.workload_image("1920x1200")
+    cores = os.cpu_count() or 1
     budget = max(0.05, 120.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_sample_rate(img, budget)
+        oracle_sample_rate(img, budget, threads=cores)
     rates, secs = [], 0.0
     cw = ch = 0
     for _ in range(args.steps):
-        r, cw, ch, dt = oracle_sample_rate(img, budget)
+        r, cw, ch, dt = oracle_sample_rate(img, budget, threads=cores)
         rates.append(r)
         secs += dt
     value = args.steps * cw * ch / secs / 1e6
     sample = (f"centred {cw}x{ch} crop of the 1920x1200 workload image per step, "
-              f"{OCTAVES}x{SUBLEVELS} levels, scale space + response + extrema, FP64 oracle")
+              f"{OCTAVES}x{SUBLEVELS} levels, scale space + response + extrema, FP64 oracle on "
+              f"{cores} host threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -450,6 +469,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = kernels[dom]["algorithmic_gbs"]
     traffic = ncu_traffic(dom)
 
+    large = None if args.no_large else run_large(args, kaze, synth, torch, flush, slowest, barrier, peak)
     describe = run_describe(args, k, torch, stream, flush, k.detect(x), slowest, barrier)
     fed = run_fed(args, kaze, torch, img, flush, slowest, barrier, t_dev_ms / args.steps)
     batched = None if args.no_batch else run_batched(args, kaze, synth, torch, stream, world, rank,
@@ -464,15 +484,15 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        rate, cw, ch, secs = oracle_sample_rate(img, args.cpu_seconds)
+        rate, secs = oracle_full_rate(img, 1)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"centred {cw}x{ch} crop of the 1920x1200 workload image, "
-                         f"{OCTAVES}x{SUBLEVELS} levels, scale space + response + extrema, "
-                         f"FP64 oracle single thread, {secs:.1f} s"}
-        arate, cores, acw, ach, asecs = oracle_all_cores_rate(img, args.cpu_seconds / 2)
+               "sample": f"the whole 1920x1200 workload image, {OCTAVES}x{SUBLEVELS} levels, scale space + "
+                         f"response + extrema, FP64 oracle on one host thread, {secs:.1f} s"}
+        cores = os.cpu_count() or 1
+        arate, asecs = oracle_full_rate(img, cores)
         cpu["all_cores"] = {"value": arate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{cores} processes, each the same centred {acw}x{ach} crop, "
-                                      f"{asecs:.1f} s wall"}
+                            "sample": f"the whole image, the oracle's independent loops on {cores} host "
+                                      f"threads, {asecs:.2f} s"}
 
     whole_bytes = detection_bytes(pixels, OCTAVES * SUBLEVELS)
     whole_gbs = whole_bytes / (t_dev_ms / args.steps * 1e-3) / 1e9
@@ -508,6 +528,15 @@ def run_ours(args, rank, world, local_rank):
                                "achieved": whole_gbs, "frac": whole_gbs / peak,
                                "model": "P (40 N - 12) bytes: 628 B/px at N = 16"}},
         "kernels": kernels,
+        # compact scalars of the side sections, beside their full records
+        "whole_frac": whole_gbs / peak,
+        "large_mpix_per_s": large["mpix_per_s"] if large else None,
+        "large_frac": large["roofline_whole"]["frac"] if large else None,
+        "batched_img_per_s": batched["img_per_s"] if batched else None,
+        "batched_plain_img_per_s": batched["plain_img_per_s"] if batched else None,
+        "batched_persistent_img_per_s": batched["persistent_img_per_s"] if batched else None,
+        "batched_frac": batched["roofline_whole"]["frac"] if batched else None,
+        "large": large,
         "describe": describe,
         "fed": fed,
         "batched": batched,
@@ -519,6 +548,45 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
     k.close()
     return 0
+
+
+def run_large(args, kaze, synth, torch, flush, max_over_ranks, barrier, peak):
+    """The 4096x3072 workload image with its sinusoidal texture (4 x 4
+    levels, scale space + detector, the keypoints copied back): Mpixel/s
+    device-resident, timed like the main line, and the whole-detection
+    fraction of the HBM roofline for its P (40 N - 12) bytes."""
+    W, H = 4096, 3072
+    img = synth.workload_image("4096x3072")
+    k = kaze.Kaze(W, H, octaves=OCTAVES, sublevels=SUBLEVELS)
+    x = torch.from_numpy(img).cuda()
+    for _ in range(max(3, min(args.warmup, 5))):
+        k.detect(x)
+    n_kp = len(k.detect(x))
+    reps = max(3, min(args.steps, 20))
+    st = k.stream
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    barrier()
+    with torch.cuda.stream(st):
+        for i in range(reps):
+            flush.zero_()
+            starts[i].record(st)
+            k.detect_enqueue(x)
+            ends[i].record(st)
+            k.detect_collect()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / reps)
+    launches = k.last_launch_count()
+    kinds = {name: n for name, (t, n) in k.profile(x).items() if n}
+    k.close()
+    byts = detection_bytes(W * H, OCTAVES * SUBLEVELS)
+    gbs = byts / (ms * 1e-3) / 1e9
+    return {"workload": "4096x3072 float32 image with sinusoidal texture, 4 octaves x 4 sublevels",
+            "ms_per_step": ms, "mpix_per_s": W * H / (ms * 1e-3) / 1e6, "keypoints": n_kp,
+            "launches_per_step": launches, "kernels": kinds,
+            "roofline_whole": {"algorithmic_bytes": byts, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                               "frac": gbs / peak},
+            "l2": "flushed before every step"}
 
 
 def run_fed(args, kaze, torch, img, flush, max_over_ranks, barrier, aos_ms):
@@ -685,7 +753,11 @@ def run_batched(args, kaze, synth, torch, stream, world, rank, max_over_ranks, b
     img_s = world * 64 * reps / (t_batch * 1e-3)
     plain_s = world * 64 / (t_plain * 1e-3)
     mode = "persistent" if tuning[0] == kaze.BATCH_PERSISTENT else "concurrent"
+    batch_bytes = sum(detection_bytes(w * h, n_levels) for w, h in sizes)
     return {"images": 64, "megapixels": round(mpx, 3), "img_per_s": img_s,
+            "roofline_whole": {"algorithmic_bytes": batch_bytes,
+                               "achieved": batch_bytes / (t_batch / reps * 1e-3) / 1e9,
+                               "frac": batch_bytes / (t_batch / reps * 1e-3) / 1e9 / measured_hbm_peak()[0]},
             "mpix_per_s": img_s * mpx / 64, "ms_per_batch": t_batch / reps,
             "plain_img_per_s": plain_s, "plain_ms_per_64": t_plain,
             "speedup_vs_plain": img_s / plain_s,
@@ -734,6 +806,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 4096x3072 section")
     ap.add_argument("--only", choices=["describe", "fed"], default=None,
                     help="run one side section alone on the workload image (profiling cases)")
     args = ap.parse_args()
