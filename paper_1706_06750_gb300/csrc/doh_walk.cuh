@@ -18,10 +18,10 @@ constexpr int DOH_WK = 24;  // outputs per walker (consecutive lattice rows)
 constexpr int DOH_DPD = 4;  // lattice rows of loads kept in flight
 
 // ld(ptr) loads one float (the read-only path for a level written by an
-// earlier launch).
-template <typename Load>
+// earlier launch); emit(j, v) sees the walker's j-th response.
+template <typename Load, typename Emit>
 __device__ __forceinline__ void doh_walk(const float* __restrict__ L, float* __restrict__ D, int pitch, int w, int h,
-                                         int s, float scale, int x, int py, int k0, Load ld)
+                                         int s, float scale, int x, int py, int k0, Load ld, Emit emit)
 {
     int cx[5];
 #pragma unroll
@@ -55,7 +55,9 @@ __device__ __forceinline__ void doh_walk(const float* __restrict__ L, float* __r
         if (m < 4) continue;
         const int y = py + s * (k0 + m - 4);
         if (y >= h) break;
-        D[(unsigned)(y * pitch + x)] = doh_value(hd, hs, hx, scale);
+        const float r = doh_value(hd, hs, hx, scale);
+        D[(unsigned)(y * pitch + x)] = r;
+        emit(m - 4, r);
     }
 }
 

@@ -56,6 +56,10 @@ struct kaze_handle {
     unsigned int* d_hmax = nullptr;
     unsigned int* d_hist = nullptr;
     unsigned int* d_count = nullptr;
+    unsigned long long* d_cand = nullptr;  // pixels the response launch found above the threshold
+    unsigned int* d_cand_count = nullptr;
+    unsigned int cand_cap = 0;
+    const float* cand_doh = nullptr;  // the response stack the list was made from
     int* d_status = nullptr;         // bit 0: a bounded device wait ran out
     float* d_exchange = nullptr;     // segment records of the resident evolution
     unsigned int* d_barrier = nullptr;  // its grid-barrier counter
@@ -372,21 +376,41 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
     return KAZE_OK;
 }
 
+// The candidate list the response launch fills for the extremum launch.
+kz::Candidates candidates(const kaze_handle* h)
+{
+    kz::Candidates c;
+    c.list = h->d_cand;
+    c.count = h->d_cand_count;
+    c.cap = h->cand_cap;
+    c.thr = h->opt.dthreshold;
+    c.lo = 1;
+    c.hi = h->N - 2;
+    return c;
+}
+
 kaze_status enqueue_response(kaze_handle* h)
 {
+    const kz::Candidates c = candidates(h);
+    KZ_TRY(h, cudaMemsetAsync(c.count, 0, sizeof(unsigned int), h->stream));
     KZ_LAUNCH_N(h, KK_DOH, kz::doh_launches(h->tab, 0, h->N),
                 kz::launch_doh(h->levels, h->doh, h->cur_pitch, h->cur_plane, h->cur_w, h->cur_h, 0, h->N, h->tab,
-                               h->stream));
+                               h->stream, &c));
+    h->cand_doh = h->doh;
     h->responded = true;
     return KAZE_OK;
 }
 
+// With `listed`, D is the handle's response stack just computed by
+// enqueue_response, whose candidate list the extremum launch visits.
 kaze_status enqueue_extrema(kaze_handle* h, const float* D, int pitch, long long plane, int w, int hh, int n,
-                            const kz::LevelTable& tab)
+                            const kz::LevelTable& tab, bool listed)
 {
+    const kz::Candidates c = candidates(h);
     KZ_TRY(h, cudaMemsetAsync(h->d_count, 0, sizeof(unsigned int), h->stream));
     KZ_LAUNCH_N(h, KK_EXTREMA, n >= 3 ? 1 : 0, kz::launch_extrema(D, pitch, plane, w, hh, n, tab, h->opt.dthreshold, h->opt.edge_r, h->d_kp,
-                                 h->opt.max_keypoints, h->d_count, h->stream));
+                                 h->opt.max_keypoints, h->d_count, h->stream,
+                                 listed && D == h->cand_doh ? &c : nullptr));
     KZ_TRY(h, cudaMemcpyAsync(h->h_count, h->d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
     KZ_TRY(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     // the first kp_pre keypoint slots go with the count, so that a detection
@@ -443,7 +467,7 @@ kaze_status run_detect_graph(kaze_handle* h, const float* d_img, int w, int hh, 
         h->launches = 0;
         KZ_CHECK(enqueue_build(h, d_img, w, hh, pitch));
         KZ_CHECK(enqueue_response(h));
-        return enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab);
+        return enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab, true);
     }
     int slot = -1;
     for (int i = 0; i < 2; ++i) {
@@ -460,7 +484,7 @@ kaze_status run_detect_graph(kaze_handle* h, const float* d_img, int w, int hh, 
         KZ_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         kaze_status s = enqueue_build(h, d_img, w, hh, pitch);
         if (s == KAZE_OK) s = enqueue_response(h);
-        if (s == KAZE_OK) s = enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab);
+        if (s == KAZE_OK) s = enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab, true);
         cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
         if (s != KAZE_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -511,9 +535,10 @@ kaze_status handle_enqueue_into(kaze_handle* h, const float* d_img, int w, int h
     h->levels = own_levels;
     h->doh = own_doh;
     KZ_CHECK(s);
+    const kz::Candidates c = candidates(h);  // filled by enqueue_response from `doh`
     KZ_TRY(h, cudaMemsetAsync(d_count, 0, sizeof(unsigned int), h->stream));
     KZ_LAUNCH_N(h, KK_EXTREMA, h->N >= 3 ? 1 : 0, kz::launch_extrema(doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab,
-                                                h->opt.dthreshold, h->opt.edge_r, d_kp, cap, d_count, h->stream));
+                                                h->opt.dthreshold, h->opt.edge_r, d_kp, cap, d_count, h->stream, &c));
     h->built = false;  // the handle's own buffers were not written
     h->responded = false;
     return KAZE_OK;
@@ -655,6 +680,11 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     const size_t off_hmax = bytes;   bytes += al(sizeof(unsigned int));
     const size_t off_hist = bytes;   bytes += al(sizeof(unsigned int) * (o.nbins + 1));  // + a block counter
     const size_t off_cnt = bytes;    bytes += al(sizeof(unsigned int));
+    // candidates of the extremum test: a sixteenth of the pixels of all
+    // levels (more falls back to the full scan)
+    const unsigned cand_cap = (unsigned)std::min<size_t>(std::max<size_t>((size_t)N * pm / 16, 65536), 1u << 30);
+    const size_t off_cand = bytes;   bytes += al(sizeof(unsigned long long) * cand_cap);
+    const size_t off_ccnt = bytes;   bytes += al(sizeof(unsigned int));
     const size_t off_status = bytes; bytes += al(sizeof(int));
     const size_t off_kp = bytes;     bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
     const size_t off_dkp = bytes;    bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
@@ -680,6 +710,9 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     h->d_hmax = (unsigned int*)(a + off_hmax);
     h->d_hist = (unsigned int*)(a + off_hist);
     h->d_count = (unsigned int*)(a + off_cnt);
+    h->d_cand = (unsigned long long*)(a + off_cand);
+    h->d_cand_count = (unsigned int*)(a + off_ccnt);
+    h->cand_cap = cand_cap;
     h->d_status = (int*)(a + off_status);
     h->d_kp = (kaze_keypoint*)(a + off_kp);
     h->d_dkp = (kaze_keypoint*)(a + off_dkp);
@@ -794,7 +827,7 @@ KAZE_API kaze_status kaze_find_extrema(kaze_handle* h, kaze_keypoint* h_out, int
 {
     if (!h || capacity < 0 || (capacity > 0 && !h_out)) return fail(h, KAZE_ERR_INVALID_ARG, "bad output");
     if (!h->responded) return fail(h, KAZE_ERR_STATE, "no detector response computed yet");
-    KZ_CHECK(enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, h->cur_w, h->cur_h, h->N, h->tab));
+    KZ_CHECK(enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, h->cur_w, h->cur_h, h->N, h->tab, true));
     return collect_keypoints(h, h_out, capacity, count);
 }
 
@@ -1150,7 +1183,7 @@ KAZE_API kaze_status kaze_op_extrema(kaze_handle* h, const float* d_D, int pitch
         t.sigma[i] = h_sigma[i];
         t.xr[i] = cross_radius(h->opt, step_of(h_sigma[i]));
     }
-    KZ_CHECK(enqueue_extrema(h, d_D, pitch, plane_stride, w, hh, n, t));
+    KZ_CHECK(enqueue_extrema(h, d_D, pitch, plane_stride, w, hh, n, t, false));
     return collect_keypoints(h, h_out, capacity, count);
 }
 
@@ -1245,7 +1278,7 @@ KAZE_API kaze_status kaze_profile(kaze_handle* h, const float* d_img, int w, int
     if (capture) KZ_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     kaze_status s = enqueue_build(h, d_img, w, hh, pitch_elems);
     if (s == KAZE_OK) s = enqueue_response(h);
-    if (s == KAZE_OK) s = enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab);
+    if (s == KAZE_OK) s = enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab, true);
     h->profiling = false;
     cudaError_t e = cudaSuccess;
     if (capture) {

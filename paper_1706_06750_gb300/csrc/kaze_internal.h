@@ -222,17 +222,33 @@ cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int 
                           unsigned int* barrier, int* status, cudaStream_t st, const EvolveFront* front = nullptr,
                           long long wait_limit = 0, int stall_tile = -1);
 
+// The pixels the extremum test of Sec. III-2 can accept: response above the
+// threshold, on a level in [lo, hi] (1 .. N-2), one pixel or more inside the
+// image.  The response kernel appends them as (level << 48 | y << 24 | x);
+// the extremum kernel then visits only those, and scans every pixel when more
+// than `cap` were found (*count > cap).  *count is zeroed before the response
+// launch.
+struct Candidates {
+    unsigned long long* list = nullptr;
+    unsigned int* count = nullptr;
+    unsigned int cap = 0;
+    float thr = 0.f;
+    int lo = 1, hi = 0;
+};
+
 // Detector response of Eq. 8 for levels [l0, l0 + nl) of a level stack.
 // Number of kernels launch_doh issues for levels l0 .. l0 + nl - 1.
 int doh_launches(const LevelTable& tab, int l0, int nl);
 cudaError_t launch_doh(const float* L, float* D, int pitch, long long plane_stride,
-                       int w, int h, int l0, int nl, const LevelTable& tab, cudaStream_t st);
+                       int w, int h, int l0, int nl, const LevelTable& tab, cudaStream_t st,
+                       const Candidates* cand = nullptr);
 
-// 3x3x3 maxima on levels [1, n-2] of a response stack.
+// 3x3x3 maxima on levels [1, n-2] of a response stack (with `cand`: the
+// pixels the response launch listed).
 cudaError_t launch_extrema(const float* D, int pitch, long long plane_stride, int w, int h,
                            int n, const LevelTable& tab, float dthreshold, float edge_r,
                            kaze_keypoint* d_kp, int cap, unsigned int* d_count,
-                           cudaStream_t st);
+                           cudaStream_t st, const Candidates* cand = nullptr);
 
 // FED (Eq. 5): the step sizes of one cycle reaching stopping time dt with
 // stability limit tau_max (the smallest n whose cycle time tau_max (n^2+n)/3

@@ -217,6 +217,24 @@ def test_extrema_step_on_identical_responses(kz):
     assert md < 1e-4
 
 
+@pytest.mark.parametrize("thr", [0.001, 1e-9])
+def test_listed_extrema_equal_the_full_scan(kz, thr):
+    """After the response launch the extremum launch visits only the pixels it
+    listed (above the threshold, one pixel inside, levels 1 .. N-2); with a
+    threshold so low that the list overflows (over 65536 entries here) it
+    scans every pixel.  Either way the keypoints are exactly those of the full
+    scan of the same responses (kaze_op_extrema)."""
+    img = synth.workload_image("256x256")
+    with kz.Kaze(256, 256, octaves=2, sublevels=4, dthreshold=thr, max_keypoints=1 << 16) as k:
+        kp = k.detect(dev(img))
+        D = k.responses().clone()
+        sig = [k.level_sigma(i) for i in range(8)]
+        kp_full = k.op_extrema(D, sig)
+        if thr < 1e-6:
+            assert int((D[1:7, 1:-1, 1:-1] > thr).sum()) > 65536
+    assert len(kp) > 20 and np.array_equal(kp, kp_full)
+
+
 # -------------------------------------------------------------- pipeline --
 
 def run_pipeline(kz, img, octaves, sublevels, k_override=0.0, **kw):
