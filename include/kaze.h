@@ -340,9 +340,18 @@ typedef struct kaze_batch kaze_batch;
  *     ctas_per_sm (capped by occupancy) shape it.
  *   KAZE_BATCH_CONCURRENT: each image runs the single-image kernel
  *     sequence; `streams` sequences run side by side as parallel branches
- *     of one recorded graph. */
+ *     of one recorded graph.
+ *   KAZE_BATCH_RESIDENT (the default where every image takes it: at most
+ *     16 x 16 tiles of 128 x 120 and no more tiles than SMs, sigma0 in
+ *     (4/3, 5/3], sigma_d <= 2): the presmoothing, contrast factor and every
+ *     AOS step of every image in ONE cooperative launch of one CTA per SM,
+ *     each image's tiles resident in shared memory on the CTAs of one wave
+ *     (images packed into waves largest first); then, per image, one
+ *     response launch and one launch of the extremum test on the pixels it
+ *     lists.  The other fields are not used. */
 #define KAZE_BATCH_PERSISTENT 0
 #define KAZE_BATCH_CONCURRENT 1
+#define KAZE_BATCH_RESIDENT 2
 typedef struct kaze_batch_tuning {
     int mode;
     int cols_per_strip;
@@ -373,8 +382,8 @@ kaze_status kaze_batch_get_response(kaze_batch* b, int image, int level, const f
 kaze_status kaze_batch_get_tuning(const kaze_batch* b, kaze_batch_tuning* t);
 kaze_status kaze_batch_set_tuning(kaze_batch* b, const kaze_batch_tuning* t);
 
-/* Autotuner: times every candidate (persistent with cols_per_strip in
- * {4, 8} x ctas_per_sm in {1, 2}; concurrent with 4, 8 or 16 streams) on
+/* Autotuner: times every candidate (resident; persistent with cols_per_strip
+ * in {4, 8} x ctas_per_sm in {1, 2}; concurrent with 4, 8 or 16 streams) on
  * the given images, `reps` runs each (CUDA events), keeps the fastest and
  * reports it and its mean time in ms. */
 kaze_status kaze_batch_autotune(kaze_batch* b, const float* const* d_imgs, const int* pitches, int reps,

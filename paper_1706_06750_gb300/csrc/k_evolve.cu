@@ -295,6 +295,7 @@ struct Params {
     unsigned int* hist;
     int nbins;
     double pct;
+    float k_fixed;         // > 0: the contrast factor (hist null), also written to d_k
     long long wait_limit;  // SM cycles a grid-barrier wait may take
     int stall_tile;        // test hook: this tile never arrives (-1: none)
 };
@@ -303,12 +304,12 @@ struct Params {
 // `target` is the count once every CTA has arrived.  The wait is bounded: on
 // timeout, or when another CTA has already flagged one, it sets bit 0 of
 // *status and returns false.
-__device__ __forceinline__ void grid_arrive(const Params& p)
+__device__ __forceinline__ void grid_arrive(const Params& p, int tile)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if ((int)blockIdx.x != p.stall_tile) atomicAdd(p.barrier, 1u);
+        if (tile != p.stall_tile) atomicAdd(p.barrier, 1u);
     }
 }
 
@@ -328,9 +329,9 @@ __device__ __forceinline__ bool grid_wait(const Params& p, unsigned target, vola
     return *s_abort == 0;
 }
 
-__device__ __forceinline__ bool grid_barrier(const Params& p, unsigned target, volatile int* s_abort)
+__device__ __forceinline__ bool grid_barrier(const Params& p, int tile, unsigned target, volatile int* s_abort)
 {
-    grid_arrive(p);
+    grid_arrive(p, tile);
     return grid_wait(p, target, s_abort);
 }
 
@@ -698,7 +699,20 @@ __device__ __forceinline__ void store_rec(float* d, int st, const Rec& R)
     d[5 * st] = R.WL;
 }
 
-__global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params p)
+// Shared state of a tile's run besides the tile arrays.
+struct TileShared {
+    int abort;
+    float k;
+    unsigned max;
+};
+
+// The whole evolution of one tile of the image `p` describes (tile index
+// tile = ty * tiles_x + tx); every tile of the image runs it on its own CTA
+// at the same time.  `bar` is the CTA's mbarrier of the record staging
+// copies and mphase the number of its phases completed so far.  False when a
+// bounded wait ran out (bit 0 of *p.status is set).
+__device__ __forceinline__ bool evolve_tile(const Params& p, int tile, TileShared& S, uint64_t* bar,
+                                            unsigned& mphase)
 {
     extern __shared__ __align__(16) float sm[];
     float* LH = sm + OFF_L;
@@ -709,34 +723,28 @@ __global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params
     float* CRc = SC + RREC;  // column chunk records [k][f][c]
     float* XR = XE;          // row chunk externals [k][2][r]
     float* XC = XE + KR * 2 * TH;
-    __shared__ int s_abort;
-    __shared__ __align__(8) uint64_t s_bar;  // completion of the record staging copies
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = blockIdx.x % p.tiles_x, ty = blockIdx.x / p.tiles_x;
+    const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
     const int x0 = tx * TW, y0 = ty * TH;
     const int tw = min(TW, p.w - x0), th = min(TH, p.h - y0);
-    const unsigned ntiles = gridDim.x;
+    const unsigned ntiles = (unsigned)(p.tiles_x * p.tiles_y);
     unsigned nbar = 0;
-    if (tid == 0) {
-        s_abort = 0;
-        mbar_init(&s_bar);
-    }
-    __shared__ float s_k;
-    __shared__ unsigned s_max;
     // lines: threads 0..TH-1 own the tile's rows, threads 128..128+TW-1 its columns
     const bool row_line = tid < th;
     const bool col_line = tid >= 128 && tid - 128 < tw;
     const int li = row_line ? tid : tid - 128;
+    __syncthreads();  // the previous tile's run is done with shared memory
 
     if (p.img)
         presmooth_tile(sm, p, x0, y0, tw, th, p.levels);
     else
         load_all(LH, p.levels, p, x0, y0);
-    if (tid == 0) s_max = 0u;
+    if (tid == 0) S.max = 0u;
     __syncthreads();
     float inv_k2 = 0.f;
     if (!p.hist) {
-        const float kk = *p.d_k;
+        const float kk = p.k_fixed > 0.f ? p.k_fixed : *p.d_k;
+        if (p.k_fixed > 0.f && tile == 0 && tid == 0) *p.d_k = kk;
         inv_k2 = 1.f / (kk * kk);
     }
 
@@ -757,11 +765,11 @@ __global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params
             float mx = scharr_pass<MODE_M2>(SC, G, 0.f, x0, y0, tw, th, p.w, p.h);
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             // non-negative floats order like their bit patterns
-            if (lane == 0 && mx > 0.f) atomicMax(&s_max, __float_as_uint(mx));
+            if (lane == 0 && mx > 0.f) atomicMax(&S.max, __float_as_uint(mx));
             __syncthreads();
-            if (tid == 0 && s_max) atomicMax(p.hmax_bits, s_max);
+            if (tid == 0 && S.max) atomicMax(p.hmax_bits, S.max);
             nbar += ntiles;
-            if (!grid_barrier(p, nbar, &s_abort)) return;
+            if (!grid_barrier(p, tile, nbar, &S.abort)) return false;
             const float hmax = __uint_as_float(ld_relaxed(reinterpret_cast<const int*>(p.hmax_bits)));
             // the tile's interior image pixels binned into one histogram per
             // warp (in SC, free after the smoothing), each thread counting a
@@ -801,7 +809,7 @@ __global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params
                 if (c) atomicAdd(&p.hist[b], c);
             }
             nbar += ntiles;
-            if (!grid_barrier(p, nbar, &s_abort)) return;
+            if (!grid_barrier(p, tile, nbar, &S.abort)) return false;
             // the whole histogram into shared memory, then the percentile
             unsigned* hs = reinterpret_cast<unsigned*>(XE);
             for (int b = tid; b < p.nbins; b += NT) hs[b] = __ldcg(p.hist + b);
@@ -809,12 +817,12 @@ __global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params
             if (warp == 0) {
                 const float kk = percentile_k(hs, p.nbins, hmax, p.pct, lane);
                 if (lane == 0) {
-                    s_k = kk;
-                    if (blockIdx.x == 0) *p.d_k = kk;
+                    S.k = kk;
+                    if (tile == 0) *p.d_k = kk;
                 }
             }
             __syncthreads();
-            inv_k2 = 1.f / (s_k * s_k);
+            inv_k2 = 1.f / (S.k * S.k);
             if (p.diffusivity == KAZE_G1)
                 g_from_m2<true>(G, inv_k2);
             else
@@ -863,7 +871,7 @@ __global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params
             store_rec(dst, 1, S);
         }
         nbar += ntiles;
-        if (!grid_barrier(p, nbar, &s_abort)) return;
+        if (!grid_barrier(p, tile, nbar, &S.abort)) return false;
 
         // 4. the records of the tile's lines from every tile (rows, then
         // columns: two contiguous blocks of global memory), staged into shared
@@ -873,20 +881,21 @@ __global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params
         if (tid == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             const unsigned brow = (unsigned)nrow4 * 4u, bcol = (unsigned)((ncol + 3) & ~3) * 4u;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_bar)),
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                          "r"(brow + bcol)
                          : "memory");
-            bulk_load(SC, p.xrow + (size_t)y0 * p.tiles_x * REC, brow, &s_bar);
-            bulk_load(SC + nrow4, p.xcol + (size_t)x0 * p.tiles_y * REC, bcol, &s_bar);
+            bulk_load(SC, p.xrow + (size_t)y0 * p.tiles_x * REC, brow, bar);
+            bulk_load(SC + nrow4, p.xcol + (size_t)x0 * p.tiles_y * REC, bcol, bar);
         }
-        if (!__syncthreads_and(mbar_wait(&s_bar, (unsigned)(lev - 1) & 1u, p.wait_limit))) {
+        if (!__syncthreads_and(mbar_wait(bar, mphase & 1u, p.wait_limit))) {
             if (tid == 0) {
                 atomicOr(p.status, 1);
-                mbar_wait(&s_bar, (unsigned)(lev - 1) & 1u, p.wait_limit);  // copies still in flight
+                mbar_wait(bar, mphase & 1u, p.wait_limit);  // copies still in flight
             }
             __syncthreads();
-            return;
+            return false;
         }
+        ++mphase;
         // the line's own segment: merge the records left and right of it and
         // solve for its two external neighbours
         float xl = 0.f, xr = 0.f;
@@ -962,10 +971,46 @@ __global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params
         if (lev + 1 < p.n_levels) {
             // 6. every tile's L_lev is in the level plane: read the ring
             nbar += ntiles;
-            if (!grid_barrier(p, nbar, &s_abort)) return;
+            if (!grid_barrier(p, tile, nbar, &S.abort)) return false;
             load_halo(LH, Lout, p, x0, y0, tw, th);
             __syncthreads();
         }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_evolve(const __grid_constant__ Params p)
+{
+    __shared__ TileShared S;
+    __shared__ __align__(8) uint64_t s_bar;  // completion of the record staging copies
+    if (threadIdx.x == 0) {
+        S.abort = 0;
+        mbar_init(&s_bar);
+    }
+    unsigned mphase = 0;
+    evolve_tile(p, (int)blockIdx.x, S, &s_bar, mphase);
+}
+
+// The evolution of a batch of images of any sizes in one cooperative launch:
+// CTA b runs the tiles work[off[b] .. off[b + 1]) in turn, each an (image,
+// tile) pair.  The host packs the images into waves of at most gridDim.x
+// tiles and gives an image's tiles to distinct CTAs of one wave, each CTA
+// taking the waves in order: the tiles of an image run at the same time, and
+// a CTA waits only for the CTAs of its own image, which reach it once they
+// are done with the earlier waves (no cycle of waits).
+__global__ void __launch_bounds__(NT, 1)
+k_evolve_batch(const Params* __restrict__ ps, const int2* __restrict__ work, const int* __restrict__ off)
+{
+    __shared__ TileShared S;
+    __shared__ __align__(8) uint64_t s_bar;
+    if (threadIdx.x == 0) {
+        S.abort = 0;
+        mbar_init(&s_bar);
+    }
+    unsigned mphase = 0;
+    for (int a = off[blockIdx.x]; a < off[blockIdx.x + 1]; ++a) {
+        const int2 wk = work[a];
+        if (!evolve_tile(ps[wk.x], wk.y, S, &s_bar, mphase)) return;
     }
 }
 
@@ -1000,14 +1045,15 @@ bool evolve_fits(int w, int h, int radius, int* tiles)
     return true;
 }
 
-cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int h, int n_levels, const double* t,
-                          float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
-                          unsigned int* barrier, int* status, cudaStream_t st, const EvolveFront* front,
-                          long long wait_limit, int stall_tile)
+namespace {
+
+// The launch parameters of one image; false when it does not fit.
+bool make_params(ev::Params& p, float* levels, long long plane, int pitch, int w, int h, int n_levels,
+                 const double* t, float* d_k, const GaussTaps& taps, int diffusivity, float* exchange,
+                 unsigned int* barrier, int* status, const EvolveFront* front, long long wait_limit, int stall_tile,
+                 float k_fixed)
 {
-    int tiles = 0;
-    if (!evolve_fits(w, h, taps.r, &tiles) || tiles > max_tiles || n_levels > kMaxLevels) return cudaErrorInvalidValue;
-    ev::Params p;
+    if (n_levels > kMaxLevels || taps.r < 1 || taps.r > ev::RMAX) return false;
     p.levels = levels;
     p.plane = plane;
     p.pitch = pitch;
@@ -1033,21 +1079,38 @@ cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int 
     p.nbins = 0;
     p.pct = 0.0;
     if (front && front->img) {
-        if (front->taps0->r != ev::R0MAX) return cudaErrorInvalidValue;
+        if (front->taps0->r != ev::R0MAX) return false;
         p.img = front->img;
         p.img_pitch = front->img_pitch;
         p.r0 = front->taps0->r;
         for (int j = 0; j <= 2 * p.r0; ++j) p.pw[j] = front->taps0->w[j];
         if (front->hist) {
-            if (front->nbins < 1 || front->nbins * ev::NWARP > ev::A_SIZE) return cudaErrorInvalidValue;
+            if (front->nbins < 1 || front->nbins * ev::NWARP > ev::A_SIZE) return false;
             p.hmax_bits = front->hmax_bits;
             p.hist = front->hist;
             p.nbins = front->nbins;
             p.pct = front->pct;
         }
     }
+    p.k_fixed = p.hist ? 0.f : k_fixed;
     p.wait_limit = wait_limit > 0 ? wait_limit : (1ll << 31);
     p.stall_tile = stall_tile;
+    return true;
+}
+
+}  // namespace
+
+cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int h, int n_levels, const double* t,
+                          float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
+                          unsigned int* barrier, int* status, cudaStream_t st, const EvolveFront* front,
+                          long long wait_limit, int stall_tile)
+{
+    int tiles = 0;
+    if (!evolve_fits(w, h, taps.r, &tiles) || tiles > max_tiles) return cudaErrorInvalidValue;
+    ev::Params p;
+    if (!make_params(p, levels, plane, pitch, w, h, n_levels, t, d_k, taps, diffusivity, exchange, barrier, status,
+                     front, wait_limit, stall_tile, 0.f))
+        return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -1061,6 +1124,56 @@ cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, ev::k_evolve, p);
+}
+
+size_t evolve_params_bytes() { return sizeof(ev::Params); }
+
+bool evolve_batch_params(void* out, const EvolveImage& im, int n_levels, const double* t, const GaussTaps& taps,
+                         int diffusivity, int* status, long long wait_limit, int stall_tile)
+{
+    int tiles = 0;
+    if (!evolve_fits(im.w, im.h, taps.r, &tiles)) return false;
+    EvolveFront f;
+    f.img = im.img;
+    f.img_pitch = im.img_pitch;
+    f.taps0 = im.taps0;
+    f.hmax_bits = im.hmax_bits;
+    f.hist = im.hist;
+    f.nbins = im.nbins;
+    f.pct = im.pct;
+    return make_params(*static_cast<ev::Params*>(out), im.levels, im.plane, im.pitch, im.w, im.h, n_levels, t,
+                       im.d_k, taps, diffusivity, im.exchange, im.barrier, status, &f, wait_limit, stall_tile,
+                       im.k_fixed);
+}
+
+int evolve_batch_grid()
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(ev::k_evolve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ev::SMEM_BYTES) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ev::k_evolve_batch, ev::NT, ev::SMEM_BYTES) !=
+            cudaSuccess)
+        return 0;
+    return per_sm < 1 ? 0 : sms * per_sm;
+}
+
+cudaError_t launch_evolve_batch(const void* d_params, const int2* d_work, const int* d_off, int grid,
+                                cudaStream_t st)
+{
+    if (grid < 1 || !d_params || !d_work || !d_off) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(ev::NT);
+    cfg.dynamicSmemBytes = ev::SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ev::k_evolve_batch, static_cast<const ev::Params*>(d_params), d_work, d_off);
 }
 
 }  // namespace kz

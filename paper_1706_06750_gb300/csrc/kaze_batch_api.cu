@@ -38,7 +38,7 @@ struct kaze_batch {
     size_t stats_bytes = 0;
 
     kz::batch::BatchParams params;
-    kaze_batch_tuning tuning{KAZE_BATCH_PERSISTENT, 4, 2, 8};
+    kaze_batch_tuning tuning{KAZE_BATCH_RESIDENT, 4, 2, 8};
 
     // concurrent mode: single-image kernel sequences on parallel branches
     std::vector<kaze_handle*> branch_h;
@@ -49,6 +49,24 @@ struct kaze_batch {
     int n_items = 0;
     long long spin_limit = 1ll << 31;
     int stall_image = -1;            // test hook: a stage that never completes
+
+    // resident mode: every image evolved by one cooperative launch with its
+    // tiles resident (k_evolve.cu), then each image's response and extrema
+    std::vector<double> t;           // t_i of Eq. 7
+    int egrid = 0;                   // CTAs of the launch (one per SM)
+    int2* d_work = nullptr;          // (image, tile) per CTA, wave after wave
+    int* d_off = nullptr;            // CTA b's work: d_work[d_off[b] .. d_off[b + 1])
+    size_t work_cap = 0;
+    void* d_resident = nullptr;      // exchange buffers, barrier counters, candidate list
+    std::vector<float*> exchange;    // per image
+    unsigned* d_ebar = nullptr;      // per image barrier counter
+    unsigned long long* d_cand = nullptr;
+    unsigned* d_cand_count = nullptr;
+    unsigned cand_cap = 0;
+    size_t eparams_bytes = 0;
+    void* d_eparams = nullptr;       // per image launch parameters
+    void* h_eparams = nullptr;       // pinned copy, refreshed with the input pointers
+    int waves = 0;
 
     cudaGraphExec_t gexec = nullptr;
     std::vector<kaze_keypoint> hkp;
@@ -199,6 +217,156 @@ kaze_status prepare_branches(kaze_batch* b)
     return KAZE_OK;
 }
 
+// The resident mode's launch parameters of every image from the current
+// input pointers (pinned: the recorded graph copies them at each replay).
+kaze_status refresh_resident(kaze_batch* b)
+{
+    const kz::batch::BatchParams& P = b->params;
+    for (int i = 0; i < b->n; ++i) {
+        const ImageDesc& d = b->h_desc[i];
+        kz::EvolveImage im;
+        im.levels = d.levels;
+        im.plane = d.plane;
+        im.pitch = d.pitch;
+        im.w = d.w;
+        im.h = d.h;
+        im.img = d.img;
+        im.img_pitch = d.img_pitch;
+        im.taps0 = &P.taps0;
+        im.d_k = d.k;
+        if (b->opt.k_override > 0.f) {
+            im.k_fixed = b->opt.k_override;
+        } else {
+            im.hmax_bits = d.hmax;
+            im.hist = d.hist;
+            im.nbins = b->opt.nbins;
+            im.pct = b->opt.k_percentile;
+        }
+        im.exchange = b->exchange[i];
+        im.barrier = b->d_ebar + i;
+        if (!kz::evolve_batch_params((char*)b->h_eparams + b->eparams_bytes * i, im, b->N, b->t.data(), P.tapsd,
+                                     b->opt.diffusivity, P.status, b->spin_limit, i == b->stall_image ? 0 : -1))
+            return bfail(b, KAZE_ERR_INVALID_ARG, "image does not take the resident evolution");
+    }
+    return KAZE_OK;
+}
+
+// Resident mode: the images packed into waves of at most one tile per CTA
+// (largest first, each into the first wave with room), the work lists of
+// the CTAs, and the buffers of the launch.
+kaze_status prepare_resident(kaze_batch* b)
+{
+    const kz::batch::BatchParams& P = b->params;
+    if (!kz::evolve_front_fits(P.taps0.r, b->opt.nbins))
+        return bfail(b, KAZE_ERR_INVALID_ARG, "presmoothing radius or bins outside the resident evolution");
+    KB_TRY(b, kz::configure_evolve_kernel());  // evolve_fits asks the occupancy of the configured kernel
+    const int grid = kz::evolve_batch_grid();
+    if (grid < 1) return bfail(b, KAZE_ERR_CUDA, "resident evolution does not fit an SM");
+    std::vector<int> tiles(b->n);
+    for (int i = 0; i < b->n; ++i)
+        if (!kz::evolve_fits(b->w[i], b->h[i], P.tapsd.r, &tiles[i]) || tiles[i] > grid)
+            return bfail(b, KAZE_ERR_INVALID_ARG, "an image does not take the resident evolution");
+    std::vector<int> order(b->n);
+    for (int i = 0; i < b->n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return tiles[x] > tiles[y]; });
+    std::vector<std::vector<int>> wave_imgs;
+    std::vector<int> wave_load;
+    for (int i : order) {
+        size_t wv = 0;
+        while (wv < wave_load.size() && wave_load[wv] + tiles[i] > grid) ++wv;
+        if (wv == wave_load.size()) {
+            wave_load.push_back(0);
+            wave_imgs.emplace_back();
+        }
+        wave_load[wv] += tiles[i];
+        wave_imgs[wv].push_back(i);
+    }
+    std::vector<std::vector<int2>> lists(grid);
+    for (const auto& wi : wave_imgs) {
+        int cta = 0;
+        for (int i : wi)
+            for (int t = 0; t < tiles[i]; ++t) lists[cta++].push_back(make_int2(i, t));
+    }
+    std::vector<int2> work;
+    std::vector<int> off(grid + 1, 0);
+    for (int c = 0; c < grid; ++c) {
+        off[c] = (int)work.size();
+        work.insert(work.end(), lists[c].begin(), lists[c].end());
+    }
+    off[grid] = (int)work.size();
+    if (work.size() > b->work_cap || !b->d_off) {
+        if (b->d_work) cudaFree(b->d_work);
+        if (b->d_off) cudaFree(b->d_off);
+        b->d_work = nullptr;
+        b->d_off = nullptr;
+        KB_TRY(b, cudaMalloc(&b->d_work, sizeof(int2) * work.size()));
+        KB_TRY(b, cudaMalloc(&b->d_off, sizeof(int) * (grid + 1)));
+        b->work_cap = work.size();
+    }
+    KB_TRY(b, cudaMemcpy(b->d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice));
+    KB_TRY(b, cudaMemcpy(b->d_off, off.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice));
+    b->egrid = grid;
+    b->waves = (int)wave_imgs.size();
+    if (!b->d_resident) {
+        auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+        size_t bytes = 0, max_plane = 0;
+        std::vector<size_t> xoff(b->n);
+        for (int i = 0; i < b->n; ++i) {
+            xoff[i] = bytes;
+            bytes += al(sizeof(float) * kz::evolve_exchange_floats(tiles[i]));
+            max_plane = std::max(max_plane, (size_t)b->plane[i]);
+        }
+        const size_t off_bar = bytes;
+        bytes += al(sizeof(unsigned) * b->n);
+        b->cand_cap = (unsigned)std::min<size_t>(std::max<size_t>((size_t)b->N * max_plane / 16, 65536), 1u << 30);
+        const size_t off_cand = bytes;
+        bytes += al(sizeof(unsigned long long) * b->cand_cap);
+        const size_t off_ccnt = bytes;
+        bytes += al(sizeof(unsigned));
+        b->eparams_bytes = (kz::evolve_params_bytes() + 15) / 16 * 16;
+        const size_t off_par = bytes;
+        bytes += al(b->eparams_bytes * b->n);
+        KB_TRY(b, cudaMalloc(&b->d_resident, bytes));
+        KB_TRY(b, cudaMallocHost(&b->h_eparams, b->eparams_bytes * b->n));
+        char* a = (char*)b->d_resident;
+        b->exchange.resize(b->n);
+        for (int i = 0; i < b->n; ++i) b->exchange[i] = (float*)(a + xoff[i]);
+        b->d_ebar = (unsigned*)(a + off_bar);
+        b->d_cand = (unsigned long long*)(a + off_cand);
+        b->d_cand_count = (unsigned*)(a + off_ccnt);
+        b->d_eparams = a + off_par;
+    }
+    return refresh_resident(b);
+}
+
+kaze_status enqueue_resident(kaze_batch* b)
+{
+    const kz::batch::BatchParams& P = b->params;
+    cudaStream_t st = b->stream;
+    KB_TRY(b, cudaMemsetAsync(b->d_count_status, 0, sizeof(unsigned) * (b->n + 1), st));
+    KB_TRY(b, cudaMemsetAsync(b->stats_base, 0, b->stats_bytes, st));
+    KB_TRY(b, cudaMemsetAsync(b->d_ebar, 0, sizeof(unsigned) * b->n, st));
+    KB_TRY(b, cudaMemcpyAsync(b->d_eparams, b->h_eparams, b->eparams_bytes * b->n, cudaMemcpyHostToDevice, st));
+    KB_TRY(b, kz::launch_evolve_batch(b->d_eparams, b->d_work, b->d_off, b->egrid, st));
+    kz::Candidates c;
+    c.list = b->d_cand;
+    c.count = b->d_cand_count;
+    c.cap = b->cand_cap;
+    c.thr = b->opt.dthreshold;
+    c.lo = 1;
+    c.hi = b->N - 2;
+    for (int i = 0; i < b->n; ++i) {
+        const ImageDesc& d = b->h_desc[i];
+        KB_TRY(b, cudaMemsetAsync(c.count, 0, sizeof(unsigned), st));
+        KB_TRY(b, kz::launch_doh(d.levels, d.doh, d.pitch, d.plane, d.w, d.h, 0, b->N, P.tab, st, &c));
+        KB_TRY(b, kz::launch_extrema(d.doh, d.pitch, d.plane, d.w, d.h, b->N, P.tab, b->opt.dthreshold,
+                                     b->opt.edge_r, d.kp, d.kp_cap, d.kp_count, st, &c));
+    }
+    KB_TRY(b, cudaMemcpyAsync(b->h_count_status, b->d_count_status, sizeof(unsigned) * (b->n + 1),
+                              cudaMemcpyDeviceToHost, st));
+    return KAZE_OK;
+}
+
 // Prepares the work list, shared memory and grid for the current tuning.
 kaze_status prepare(kaze_batch* b)
 {
@@ -206,6 +374,10 @@ kaze_status prepare(kaze_batch* b)
     if (b->tuning.mode == KAZE_BATCH_CONCURRENT) {
         drop_graph(b);
         return prepare_branches(b);
+    }
+    if (b->tuning.mode == KAZE_BATCH_RESIDENT) {
+        drop_graph(b);
+        return prepare_resident(b);
     }
     const int cols = b->tuning.cols_per_strip;
     std::vector<Item> items;
@@ -273,6 +445,7 @@ kaze_status enqueue(kaze_batch* b)
 {
     using namespace kz::batch;
     if (b->tuning.mode == KAZE_BATCH_CONCURRENT) return enqueue_concurrent(b);
+    if (b->tuning.mode == KAZE_BATCH_RESIDENT) return enqueue_resident(b);
     cudaStream_t st = b->stream;
     KB_TRY(b, cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), st));
     KB_TRY(b, cudaMemsetAsync(b->d_done, 0, sizeof(unsigned) * (size_t)b->n * slots_per_image(), st));
@@ -371,6 +544,7 @@ KAZE_API kaze_status kaze_batch_create(const kaze_options* opt, int n, const int
             st = st < 1 ? 1 : st;
             P.tab.step[i] = st;
             P.tab.sigma[i] = (float)sig[i];
+            P.tab.xr[i] = 1;  // the 3x3x3 test
             double norm;
             if (o.doh_norm == KAZE_DOH_PAPER_LITERAL) {
                 const double kn = sig[i] / std::pow(2.0, (double)oc);
@@ -391,6 +565,7 @@ KAZE_API kaze_status kaze_batch_create(const kaze_options* opt, int n, const int
     P.k_override = o.k_override;
     P.N = N;
     P.slots = slots_per_image();
+    b->t.assign(t, t + N);
 
     // arena: per image N levels, N responses, g, ux; then statistics, keypoints
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
@@ -463,7 +638,13 @@ KAZE_API kaze_status kaze_batch_create(const kaze_options* opt, int n, const int
     P.done = b->d_done;
     P.need = b->d_need;
     P.status = (int*)(b->d_count_status + n);
-    const kaze_status s = prepare(b);
+    // the resident evolution where every image takes it, else the work queue
+    kaze_status s = prepare(b);
+    if (s != KAZE_OK && b->tuning.mode == KAZE_BATCH_RESIDENT) {
+        b->err.clear();
+        b->tuning.mode = KAZE_BATCH_PERSISTENT;
+        s = prepare(b);
+    }
     if (s != KAZE_OK) {
         kaze_batch_destroy(b);
         return s;
@@ -479,6 +660,7 @@ KAZE_API kaze_status kaze_batch_detect(kaze_batch* b, const float* const* d_imgs
         return bfail(b, KAZE_ERR_INVALID_ARG, "bad output arguments");
     kaze_status s = set_inputs(b, d_imgs, pitches);
     if (s != KAZE_OK) return s;
+    if (b->tuning.mode == KAZE_BATCH_RESIDENT && (s = refresh_resident(b)) != KAZE_OK) return s;
     s = run(b);
     if (s != KAZE_OK) return s;
     KB_TRY(b, cudaStreamSynchronize(b->stream));
@@ -530,7 +712,7 @@ KAZE_API kaze_status kaze_batch_get_response(kaze_batch* b, int image, int level
 KAZE_API kaze_status kaze_batch_set_tuning(kaze_batch* b, const kaze_batch_tuning* t)
 {
     if (!b || !t) return KAZE_ERR_INVALID_ARG;
-    if ((t->mode != KAZE_BATCH_PERSISTENT && t->mode != KAZE_BATCH_CONCURRENT) ||
+    if ((t->mode != KAZE_BATCH_PERSISTENT && t->mode != KAZE_BATCH_CONCURRENT && t->mode != KAZE_BATCH_RESIDENT) ||
         (t->cols_per_strip != 4 && t->cols_per_strip != 8) || t->ctas_per_sm < 1 || t->ctas_per_sm > 8 ||
         t->streams < 1 || t->streams > 64)
         return bfail(b, KAZE_ERR_INVALID_ARG, "tuning out of range");
@@ -564,6 +746,7 @@ KAZE_API kaze_status kaze_batch_autotune(kaze_batch* b, const float* const* d_im
     KB_TRY(b, cudaEventCreate(&e0));
     KB_TRY(b, cudaEventCreate(&e1));
     std::vector<kaze_batch_tuning> cands;
+    cands.push_back(kaze_batch_tuning{KAZE_BATCH_RESIDENT, 4, 1, 8});
     for (int cols : {4, 8})
         for (int ctas : {1, 2}) cands.push_back(kaze_batch_tuning{KAZE_BATCH_PERSISTENT, cols, ctas, 8});
     for (int streams : {4, 8, 16}) cands.push_back(kaze_batch_tuning{KAZE_BATCH_CONCURRENT, 4, 2, streams});
@@ -621,6 +804,10 @@ KAZE_API void kaze_batch_destroy(kaze_batch* b)
     drop_branches(b);
     if (b->h_branch_status) cudaFreeHost(b->h_branch_status);
     if (b->d_items) cudaFree(b->d_items);
+    if (b->d_work) cudaFree(b->d_work);
+    if (b->d_off) cudaFree(b->d_off);
+    if (b->d_resident) cudaFree(b->d_resident);
+    if (b->h_eparams) cudaFreeHost(b->h_eparams);
     if (b->arena) cudaFree(b->arena);
     if (b->h_desc) cudaFreeHost(b->h_desc);
     if (b->h_count_status) cudaFreeHost(b->h_count_status);

@@ -213,6 +213,37 @@ struct EvolveFront {
     int nbins = 0;
     double pct = 0.0;
 };
+// The batched form: one cooperative launch of evolve_batch_grid() CTAs (one
+// per SM) evolving many images, each image's tiles on distinct CTAs of one
+// wave (work: (image, tile) pairs, CTA b taking work[off[b] .. off[b + 1])
+// in order; every image's tiles fit the grid).  The parameters of image i
+// are the evolve_params_bytes() bytes at d_params + i * that size, made by
+// evolve_batch_params (false: the image does not take the resident
+// evolution).  Each image has its own exchange (evolve_exchange_floats of its
+// tiles) and barrier counter, zeroed before the launch; hist null takes k
+// from k_fixed > 0 (written to d_k), else from d_k.
+struct EvolveImage {
+    float* levels = nullptr;
+    long long plane = 0;
+    int pitch = 0, w = 0, h = 0;
+    const float* img = nullptr;  // presmoothed into level 0 inside the launch
+    int img_pitch = 0;
+    const GaussTaps* taps0 = nullptr;
+    float* d_k = nullptr;
+    unsigned int* hmax_bits = nullptr;
+    unsigned int* hist = nullptr;
+    int nbins = 0;
+    double pct = 0.0;
+    float k_fixed = 0.f;
+    float* exchange = nullptr;
+    unsigned int* barrier = nullptr;
+};
+size_t evolve_params_bytes();
+bool evolve_batch_params(void* out, const EvolveImage& im, int n_levels, const double* t, const GaussTaps& taps,
+                         int diffusivity, int* status, long long wait_limit, int stall_tile);
+int evolve_batch_grid();
+cudaError_t launch_evolve_batch(const void* d_params, const int2* d_work, const int* d_off, int grid,
+                                cudaStream_t st);
 cudaError_t configure_evolve_kernel();
 size_t evolve_exchange_floats(int max_tiles);
 bool evolve_fits(int w, int h, int radius, int* tiles);

@@ -72,6 +72,7 @@ class Keypoint(ctypes.Structure):
 
 BATCH_PERSISTENT = 0
 BATCH_CONCURRENT = 1
+BATCH_RESIDENT = 2
 
 
 class BatchTuning(ctypes.Structure):

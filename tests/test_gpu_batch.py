@@ -43,9 +43,12 @@ def single_path(kz, img, **kw):
 
 
 def test_batch_matches_single_image_path(kz):
+    """The default batch execution (the resident evolution: the same tile
+    code as the single-image launch) against the single-image path."""
     imgs = images(SIZES)
     xs = [torch.from_numpy(a).cuda() for a in imgs]
     with kz.Batch(SIZES, octaves=2, sublevels=4) as b:
+        assert b.tuning()[0] == kz.BATCH_RESIDENT
         kps = b.detect(xs)
         for i, img in enumerate(imgs):
             lv, D, kp, _ = single_path(kz, img)
@@ -58,11 +61,17 @@ def test_batch_matches_single_image_path(kz):
 
 
 @pytest.mark.parametrize("tuning", [(0, 4, 1, 8), (0, 4, 2, 8), (0, 8, 1, 8), (0, 8, 2, 8),
-                                    (1, 4, 2, 2), (1, 4, 2, 16)])
+                                    (1, 4, 2, 2), (1, 4, 2, 16), (2, 4, 1, 8)])
 def test_every_execution_shape_gives_the_same_result(kz, tuning):
+    """Against the work-queue launch with 4-column strips: the other shapes
+    of the line solvers within FP32 rounding of one another (2e-6); the
+    resident evolution (chunked spike solves) within twice the oracle
+    tolerance, as two solvers each within 2e-5 of the oracle."""
     imgs = images(SIZES, 700)
     xs = [torch.from_numpy(a).cuda() for a in imgs]
+    ltol, dtol = (4e-5, 2e-4) if tuning[0] == kz.BATCH_RESIDENT else (2e-6, 1e-5)
     with kz.Batch(SIZES, octaves=2, sublevels=4) as b:
+        b.set_tuning(kz.BATCH_PERSISTENT, 4, 2, 8)
         ref = b.detect(xs)
         L7 = [b.level(i, 7).cpu().numpy() for i in range(len(SIZES))]
         D5 = [b.response(i, 5).cpu().numpy() for i in range(len(SIZES))]
@@ -70,8 +79,8 @@ def test_every_execution_shape_gives_the_same_result(kz, tuning):
         assert b.tuning() == tuning
         got = b.detect(xs)
         for i in range(len(SIZES)):
-            assert np.max(np.abs(b.level(i, 7).cpu().numpy() - L7[i])) <= 2e-6
-            assert np.max(np.abs(b.response(i, 5).cpu().numpy() - D5[i])) <= 1e-5 * np.max(np.abs(D5[i]))
+            assert np.max(np.abs(b.level(i, 7).cpu().numpy() - L7[i])) <= ltol
+            assert np.max(np.abs(b.response(i, 5).cpu().numpy() - D5[i])) <= dtol * np.max(np.abs(D5[i]))
             a = {(int(r["level"]), int(r["iy"]), int(r["ix"])) for r in got[i]}
             e = {(int(r["level"]), int(r["iy"]), int(r["ix"])) for r in ref[i]}
             assert len(a & e) >= 0.995 * max(len(a), len(e), 1)
@@ -110,8 +119,12 @@ def test_stalled_dependency_times_out_and_the_handle_recovers(kz):
 
 
 def test_mixed_size_workload_sample(kz):
-    """The 64-image mixed-size workload: three images checked against the
-    single-image path, keypoint counts sane for all."""
+    """The 64-image mixed-size workload: the default execution (the resident
+    evolution) against the concurrent one (line solvers): two FP32 solvers,
+    each held to 99.5 % keypoint overlap with the oracle, so at least 99 %
+    with each other; three images against the single-image path (the same
+    arithmetic: no keypoint off a decision boundary may differ); keypoint
+    counts sane for all."""
     sizes = synth.batch_sizes(64)
     imgs = synth.batch_images(64)
     xs = [torch.from_numpy(a).cuda() for a in imgs]
@@ -128,7 +141,7 @@ def test_mixed_size_workload_sample(kz):
         sa = {(int(r["level"]), int(r["iy"]), int(r["ix"])) for r in a}
         sc = {(int(r["level"]), int(r["iy"]), int(r["ix"])) for r in c}
         common += len(sa & sc)
-    assert common >= 0.995 * total
+    assert common >= 0.99 * total
     # three images against the single-image path; keypoints that differ
     # must sit on a decision boundary of the response
     for i in (0, 17, 63):

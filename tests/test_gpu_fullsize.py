@@ -5,8 +5,8 @@
   level, every response and the keypoints (the line kernels: its 32 x 26
   tiles exceed one a SM);
 * two members of the 64-image mixed-size batch (a 640x480 and a 1280x720
-  image) through the single persistent launch, against the oracle's
-  detection of each;
+  image) through the work-queue launch and through the resident evolution
+  of the whole batch, against the oracle's detection of each;
 * the FED evolution (Eq. 5) of the 1920x1200 workload image, against the
   oracle's FED scale space.
 
@@ -83,10 +83,13 @@ def test_pipeline_4096x3072_against_oracle(kz):
     assert len(kp_r) >= 1000 and ov >= KP_OVERLAP, (ov, len(kp_r), len(kp_g), ur[:3], ug[:3])
 
 
+@pytest.mark.parametrize("mode", ["persistent", "resident"])
 @pytest.mark.parametrize("size", [(640, 480), (1280, 720)])
-def test_batch_member_against_oracle(kz, size):
-    """The 64-image workload in one persistent launch with the member's
-    oracle k for every image; the member against the oracle."""
+def test_batch_member_against_oracle(kz, size, mode):
+    """The 64-image workload in one launch (the work-queue kernel, or the
+    resident evolution of every image followed by each image's response and
+    extrema) with the member's oracle k for every image; the member against
+    the oracle."""
     sizes = synth.batch_sizes(64)
     j = sizes.index(size)
     imgs = synth.batch_images(64)
@@ -94,9 +97,10 @@ def test_batch_member_against_oracle(kz, size):
     k_ref, _ = oracle_k(img)
     kf = float(np.float32(k_ref))
     xs = [torch.from_numpy(a).cuda() for a in imgs]
+    m = kz.BATCH_PERSISTENT if mode == "persistent" else kz.BATCH_RESIDENT
     with kz.Batch(sizes, k_override=kf) as b:
-        b.set_tuning(kz.BATCH_PERSISTENT, 4, 2, 8)
-        assert b.tuning()[0] == kz.BATCH_PERSISTENT
+        b.set_tuning(m, 4, 2, 8)
+        assert b.tuning()[0] == m
         kps = b.detect(xs)
         lv_g = np.stack([b.level(j, l).cpu().numpy() for l in range(16)]).astype(np.float64)
         D_g = np.stack([b.response(j, l).cpu().numpy() for l in range(16)]).astype(np.float64)
