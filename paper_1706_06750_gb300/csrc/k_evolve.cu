@@ -386,37 +386,61 @@ __device__ __forceinline__ void load_all(float* LH, const float* src, const Para
 }
 
 // The LH positions outside the tile's own image pixels [0, th) x [0, tw):
-// the bands above and below (whole width), then left and right of them.
+// the bands above and below (whole width, a warp per row, lanes along it),
+// then left and right of them.  A full tile's side bands are HALO columns
+// each (element e: row e / 10, a compile-time division); a ragged tile's
+// right band is wider and takes the general enumeration.
 __device__ __forceinline__ void load_halo(float* LH, const float* src, const Params& p, int x0, int y0, int tw,
                                           int th)
 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nb = TH + HALO - th;  // rows below
     const int wr = TW + HALO - tw;  // columns right of the image part
-    const int nside = HALO + wr;
-    const int n1 = (HALO + nb) * LCOLS;
-    auto pos = [&](int e, int& rr, int& cc) {
-        if (e < n1) {
-            const int q = e / LCOLS;
-            cc = e - q * LCOLS;
-            rr = q < HALO ? q : th + HALO + (q - HALO);
-        } else {
-            const int f = e - n1, r = f / nside, q = f - r * nside;
-            rr = r + HALO;
-            cc = q < HALO ? q : tw + HALO + (q - HALO);
+    auto col = [&](int cc) { return reflect_index(x0 + cc - HALO, p.w); };
+    constexpr int NCI = (LCOLS + 31) / 32;
+    for (int q = warp; q < HALO + nb; q += NWARP) {
+        const int rr = q < HALO ? q : th + HALO + (q - HALO);
+        const float* srow = src + (size_t)reflect_index(y0 + rr - HALO, p.h) * p.pitch;
+        float v[NCI];
+#pragma unroll
+        for (int i = 0; i < NCI; ++i) {
+            const int cc = lane + 32 * i;
+            v[i] = cc < LCOLS ? __ldcg(srow + col(cc)) : 0.f;
         }
-    };
-    copy_batched<8>(
-        n1 + th * nside,
-        [&](int e) {
-            int rr, cc;
-            pos(e, rr, cc);
-            return src + (size_t)reflect_index(y0 + rr - HALO, p.h) * p.pitch + reflect_index(x0 + cc - HALO, p.w);
-        },
-        [&](int e) {
-            int rr, cc;
-            pos(e, rr, cc);
-            return LH + rr * LS + cc;
-        });
+#pragma unroll
+        for (int i = 0; i < NCI; ++i) {
+            const int cc = lane + 32 * i;
+            if (cc < LCOLS) LH[rr * LS + cc] = v[i];
+        }
+    }
+    const int nside = HALO + wr;
+    if (nside == 2 * HALO) {
+        copy_batched<4>(
+            th * 2 * HALO,
+            [&](int e) {
+                const int r = e / (2 * HALO), q = e - r * (2 * HALO);
+                const int cc = q < HALO ? q : tw + q;
+                return src + (size_t)(y0 + r) * p.pitch + col(cc);
+            },
+            [&](int e) {
+                const int r = e / (2 * HALO), q = e - r * (2 * HALO);
+                const int cc = q < HALO ? q : tw + q;
+                return LH + (r + HALO) * LS + cc;
+            });
+    } else {
+        copy_batched<4>(
+            th * nside,
+            [&](int e) {
+                const int r = e / nside, q = e - r * nside;
+                const int cc = q < HALO ? q : tw + HALO + (q - HALO);
+                return src + (size_t)(y0 + r) * p.pitch + col(cc);
+            },
+            [&](int e) {
+                const int r = e / nside, q = e - r * nside;
+                const int cc = q < HALO ? q : tw + HALO + (q - HALO);
+                return LH + (r + HALO) * LS + cc;
+            });
+    }
 }
 
 // Ghost conductance past the image (see Chunk): along rows, columns
