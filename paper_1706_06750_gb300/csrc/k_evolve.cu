@@ -473,123 +473,151 @@ __device__ __forceinline__ void ghost_conductance(float* G, int x0, int y0, int 
 }
 
 // g of Eq. 2-3 on tile rows -1..TH, columns -1..TW (into G) from LH in three
-// passes: the horizontal Gaussian pass H(r, c) = sum_j w_j L(r, c + j),
-// r in [-HALO, TH + HALO), c in [-2, TW + 2), by threads walking 44 columns
-// of one row (lanes: consecutive rows) ...
+// passes, each thread taking two lines half the tile apart with packed FP32x2
+// arithmetic (each half rounds exactly as the scalar operation, so the
+// results are those of the line-kernel path bit for bit): the horizontal
+// Gaussian pass H(r, c) = sum_j w_j L(r, c + j), r in [-HALO, TH + HALO),
+// c in [-2, TW + 2), by threads walking 22 columns of rows r and r + 65
+// (lanes: consecutive rows) ...
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 __device__ __forceinline__ void h_pass(const float* __restrict__ LH, float* __restrict__ H, const Params& p)
 {
-    const float w0 = p.wt[0], w1 = p.wt[1], w2 = p.wt[2], w3 = p.wt[3];
-    constexpr int SEG = HCOLS / 3;
-    static_assert(SEG * 3 == HCOLS && HROWS * 3 <= NT, "three row segments, one job a thread");
-    for (int job = threadIdx.x; job < HROWS * 3; job += NT) {
-        const int s = job / HROWS, rr = job - s * HROWS;
-        const int cb = -2 + SEG * s;
-        const float* src = LH + rr * LS + (cb + HALO);
-        float* dst = H + rr * HS + (cb + 2);
-        float v0 = src[-3], v1 = src[-2], v2 = src[-1], v3 = src[0], v4 = src[1], v5 = src[2];
-#pragma unroll 4
-        for (int q = 0; q < SEG; ++q) {
-            const float v6 = src[q + 3];
-            float hv = w0 * v3;
-            hv = fmaf(w1, v2 + v4, hv);
-            hv = fmaf(w2, v1 + v5, hv);
-            hv = fmaf(w3, v0 + v6, hv);
-            dst[q] = hv;
-            v0 = v1;
-            v1 = v2;
-            v2 = v3;
-            v3 = v4;
-            v4 = v5;
-            v5 = v6;
-        }
+    const float2 w0 = f2(p.wt[0], p.wt[0]), w1 = f2(p.wt[1], p.wt[1]), w2 = f2(p.wt[2], p.wt[2]),
+                 w3 = f2(p.wt[3], p.wt[3]);
+    constexpr int HALF = HROWS / 2, SEG = HCOLS / 6;
+    static_assert(HALF * 2 == HROWS && SEG * 6 == HCOLS && HALF * 6 <= NT, "two rows, six segments, one job a thread");
+    const int job = threadIdx.x;
+    if (job >= HALF * 6) return;
+    const int s = job / HALF, rr = job - s * HALF;
+    const int cb = -2 + SEG * s;
+    const float* a = LH + rr * LS + (cb + HALO);
+    const float* b = a + HALF * LS;
+    float* da = H + rr * HS + (cb + 2);
+    float* db = da + HALF * HS;
+    float2 v0 = f2(a[-3], b[-3]), v1 = f2(a[-2], b[-2]), v2 = f2(a[-1], b[-1]), v3 = f2(a[0], b[0]),
+           v4 = f2(a[1], b[1]), v5 = f2(a[2], b[2]);
+#pragma unroll 2
+    for (int q = 0; q < SEG; ++q) {
+        const float2 v6 = f2(a[q + 3], b[q + 3]);
+        float2 hv = __fmul2_rn(w0, v3);
+        hv = __ffma2_rn(w1, __fadd2_rn(v2, v4), hv);
+        hv = __ffma2_rn(w2, __fadd2_rn(v1, v5), hv);
+        hv = __ffma2_rn(w3, __fadd2_rn(v0, v6), hv);
+        da[q] = hv.x;
+        db[q] = hv.y;
+        v0 = v1;
+        v1 = v2;
+        v2 = v3;
+        v3 = v4;
+        v4 = v5;
+        v5 = v6;
     }
 }
 
 // ... then the vertical pass S, r in [-2, TH + 2), c in [-2, TW + 2), by
-// threads walking 42 rows of one column with the 7 H values in registers
-// (lanes: consecutive columns) ...
+// threads walking 21 rows of columns c and c + 66 with the 7 H values of
+// each in registers (lanes: consecutive columns) ...
 __device__ __forceinline__ void v_pass(const float* __restrict__ H, float* __restrict__ S, const Params& p)
 {
-    const float w0 = p.wt[0], w1 = p.wt[1], w2 = p.wt[2], w3 = p.wt[3];
-    constexpr int RG = (SROWS + 2) / 3;  // 42 rows a job
-    static_assert(SCOLS * 3 <= NT, "one job a thread");
-    for (int job = threadIdx.x; job < SCOLS * 3; job += NT) {
-        const int q = job / SCOLS, c = job - q * SCOLS;  // c: column + 2
-        const int r0 = q * RG, r1 = min(r0 + RG, SROWS);  // S rows r0 - 2 .. r1 - 3
-        // S row index i needs H row indices i .. i + 6
-        const float* h = H + c;
-        float h0 = h[(r0 + 0) * HS], h1 = h[(r0 + 1) * HS], h2 = h[(r0 + 2) * HS], h3 = h[(r0 + 3) * HS],
-              h4 = h[(r0 + 4) * HS], h5 = h[(r0 + 5) * HS];
-        float* o = S + c;
-#pragma unroll 4
-        for (int i = r0; i < r1; ++i) {
-            const float h6 = h[(i + 6) * HS];
-            float sv = w0 * h3;
-            sv = fmaf(w1, h2 + h4, sv);
-            sv = fmaf(w2, h1 + h5, sv);
-            sv = fmaf(w3, h0 + h6, sv);
-            o[i * SS] = sv;
-            h0 = h1;
-            h1 = h2;
-            h2 = h3;
-            h3 = h4;
-            h4 = h5;
-            h5 = h6;
-        }
+    const float2 w0 = f2(p.wt[0], p.wt[0]), w1 = f2(p.wt[1], p.wt[1]), w2 = f2(p.wt[2], p.wt[2]),
+                 w3 = f2(p.wt[3], p.wt[3]);
+    constexpr int HALF = SCOLS / 2, RG = (SROWS + 5) / 6;  // 66 column pairs, 21 rows a job
+    static_assert(HALF * 2 == SCOLS && HALF * 6 <= NT, "two columns, six segments, one job a thread");
+    const int job = threadIdx.x;
+    if (job >= HALF * 6) return;
+    const int q = job / HALF, c = job - q * HALF;  // c: column + 2
+    const int r0 = q * RG, r1 = min(r0 + RG, SROWS);  // S rows r0 - 2 .. r1 - 3
+    // S row index i needs H row indices i .. i + 6
+    const float* ha = H + c;
+    const float* hb = ha + HALF;
+    auto ld = [&](int i) { return f2(ha[i * HS], hb[i * HS]); };
+    float2 h0 = ld(r0), h1 = ld(r0 + 1), h2 = ld(r0 + 2), h3 = ld(r0 + 3), h4 = ld(r0 + 4), h5 = ld(r0 + 5);
+    float* oa = S + c;
+    float* ob = oa + HALF;
+#pragma unroll 2
+    for (int i = r0; i < r1; ++i) {
+        const float2 h6 = ld(i + 6);
+        float2 sv = __fmul2_rn(w0, h3);
+        sv = __ffma2_rn(w1, __fadd2_rn(h2, h4), sv);
+        sv = __ffma2_rn(w2, __fadd2_rn(h1, h5), sv);
+        sv = __ffma2_rn(w3, __fadd2_rn(h0, h6), sv);
+        oa[i * SS] = sv.x;
+        ob[i * SS] = sv.y;
+        h0 = h1;
+        h1 = h2;
+        h2 = h3;
+        h3 = h4;
+        h4 = h5;
+        h5 = h6;
     }
 }
 
 // ... and the 3x3 Scharr pair and g (Eq. 3) at rows -1..TH, columns -1..TW:
-// a thread walks 41 rows of one column with the D, E values of the rows
-// above in registers (the operations of the line-kernel path, in order).
-// MODE_G2 / MODE_G1 write g of Eq. 3; MODE_M2 writes |grad|^2 and returns
-// this thread's maximum of |grad| over the tile's own interior image pixels
-// (the contrast factor's maximum pass).
+// a thread walks 21 rows of columns c and c + 65 with the D, E values of the
+// rows above in registers (the operations of the line-kernel path, in
+// order; b - a as b + (-a), the same rounding).  MODE_G2 / MODE_G1 write g of
+// Eq. 3; MODE_M2 writes |grad|^2 and returns this thread's maximum of |grad|
+// over the tile's own interior image pixels (the contrast factor's maximum
+// pass).
 enum { MODE_G2 = 0, MODE_G1 = 1, MODE_M2 = 2 };
 
 template <int MODE>
 __device__ __forceinline__ float scharr_pass(const float* __restrict__ S, float* __restrict__ G, float inv_k2, int x0,
                                              int y0, int tw, int th, int w, int h)
 {
-    constexpr int RG = (GROWS + 2) / 3;  // 41 rows a job
-    static_assert(GCOLS * 3 <= NT, "one job a thread");
+    constexpr int HALF = GCOLS / 2, RG = (GROWS + 5) / 6;  // 65 column pairs, 21 rows a job
+    static_assert(HALF * 2 == GCOLS && HALF * 6 <= NT, "two columns, six segments, one job a thread");
     float mx = 0.f;
-    for (int job = threadIdx.x; job < GCOLS * 3; job += NT) {
-        const int q = job / GCOLS, cc = job - q * GCOLS;  // cc: column + 1
-        const int r0 = q * RG, r1 = min(r0 + RG, GROWS);  // g rows r0 - 1 .. r1 - 2
-        // g row gr (index gr + 1) uses S rows gr - 1 .. gr + 1 (index gr + 1 .. gr + 3)
-        const float* sc = S + cc;  // S column (cc - 1) - 1 + 2 = cc: the left neighbour
-        auto de = [&](int si, float& d, float& e) {
-            const float sl = sc[si * SS], sv = sc[si * SS + 1], sr = sc[si * SS + 2];
-            d = sr - sl;
-            e = fmaf(10.f, sv, 3.f * (sl + sr));
-        };
-        float dm, em, d0, e0;
-        de(r0, dm, em);
-        de(r0 + 1, d0, e0);
-        float* o = G + cc;
-        // interior image pixels of the tile's own column, if any (MODE_M2)
-        const int gc = cc - 1, gx = x0 + gc;
-        const bool col_in = gc >= 0 && gc < tw && gx >= 1 && gx <= w - 2;
-        const int ilo = max(1 - y0, 0) + 1, ihi = min(h - 2 - y0, th - 1) + 1;  // g row index range
-#pragma unroll 4
-        for (int i = r0; i < r1; ++i) {
-            float dp, ep;
-            de(i + 2, dp, ep);
-            const float lx = fmaf(10.f, d0, 3.f * (dm + dp)) * (1.f / 32.f);
-            const float ly = (ep - em) * (1.f / 32.f);
-            const float m2 = fmaf(ly, ly, lx * lx);
-            if (MODE == MODE_M2) {
-                o[i * GS] = m2;
-                if (col_in && i >= ilo && i <= ihi) mx = fmaxf(mx, sqrtf(m2));
-            } else {
-                o[i * GS] = MODE == MODE_G1 ? expf(-(m2 * inv_k2)) : __fdividef(1.f, fmaf(m2, inv_k2, 1.f));
+    const int job = threadIdx.x;
+    if (job >= HALF * 6) return mx;
+    const int q = job / HALF, cc = job - q * HALF;  // cc: column + 1
+    const int r0 = q * RG, r1 = min(r0 + RG, GROWS);  // g rows r0 - 1 .. r1 - 2
+    // g row gr (index gr + 1) uses S rows gr - 1 .. gr + 1 (index gr + 1 .. gr + 3)
+    const float* sa = S + cc;  // S column (cc - 1) - 1 + 2 = cc: the left neighbour
+    const float* sb = sa + HALF;
+    const float2 c10 = f2(10.f, 10.f), c3 = f2(3.f, 3.f), c32 = f2(1.f / 32.f, 1.f / 32.f);
+    auto de = [&](int si, float2& d, float2& e) {
+        const float2 sl = f2(sa[si * SS], sb[si * SS]), sv = f2(sa[si * SS + 1], sb[si * SS + 1]),
+                     sr = f2(sa[si * SS + 2], sb[si * SS + 2]);
+        d = __fadd2_rn(sr, f2(-sl.x, -sl.y));
+        e = __ffma2_rn(c10, sv, __fmul2_rn(c3, __fadd2_rn(sl, sr)));
+    };
+    float2 dm, em, d0, e0;
+    de(r0, dm, em);
+    de(r0 + 1, d0, e0);
+    float* oa = G + cc;
+    float* ob = oa + HALF;
+    // interior image pixels of the tile's own columns, if any (MODE_M2)
+    const int gca = cc - 1, gcb = cc - 1 + HALF;
+    const bool in_a = gca >= 0 && gca < tw && x0 + gca >= 1 && x0 + gca <= w - 2;
+    const bool in_b = gcb >= 0 && gcb < tw && x0 + gcb >= 1 && x0 + gcb <= w - 2;
+    const int ilo = max(1 - y0, 0) + 1, ihi = min(h - 2 - y0, th - 1) + 1;  // g row index range
+#pragma unroll 2
+    for (int i = r0; i < r1; ++i) {
+        float2 dp, ep;
+        de(i + 2, dp, ep);
+        const float2 lx = __fmul2_rn(__ffma2_rn(c10, d0, __fmul2_rn(c3, __fadd2_rn(dm, dp))), c32);
+        const float2 ly = __fmul2_rn(__fadd2_rn(ep, f2(-em.x, -em.y)), c32);
+        const float2 m2 = __ffma2_rn(ly, ly, __fmul2_rn(lx, lx));
+        if (MODE == MODE_M2) {
+            oa[i * GS] = m2.x;
+            ob[i * GS] = m2.y;
+            if (i >= ilo && i <= ihi) {
+                if (in_a) mx = fmaxf(mx, sqrtf(m2.x));
+                if (in_b) mx = fmaxf(mx, sqrtf(m2.y));
             }
-            dm = d0;
-            d0 = dp;
-            em = e0;
-            e0 = ep;
+        } else if (MODE == MODE_G1) {
+            oa[i * GS] = expf(-(m2.x * inv_k2));
+            ob[i * GS] = expf(-(m2.y * inv_k2));
+        } else {
+            oa[i * GS] = __fdividef(1.f, fmaf(m2.x, inv_k2, 1.f));
+            ob[i * GS] = __fdividef(1.f, fmaf(m2.y, inv_k2, 1.f));
         }
+        dm = d0;
+        d0 = dp;
+        em = e0;
+        e0 = ep;
     }
     return mx;
 }
