@@ -1155,7 +1155,7 @@ bool make_params(ev::Params& p, float* levels, long long plane, int pitch, int w
 cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int h, int n_levels, const double* t,
                           float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
                           unsigned int* barrier, int* status, cudaStream_t st, const EvolveFront* front,
-                          long long wait_limit, int stall_tile)
+                          long long wait_limit, int stall_tile, bool zero_barrier)
 {
     int tiles = 0;
     if (!evolve_fits(w, h, taps.r, &tiles) || tiles > max_tiles) return cudaErrorInvalidValue;
@@ -1163,8 +1163,10 @@ cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int 
     if (!make_params(p, levels, plane, pitch, w, h, n_levels, t, d_k, taps, diffusivity, exchange, barrier, status,
                      front, wait_limit, stall_tile, 0.f))
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), st);
-    if (e != cudaSuccess) return e;
+    if (zero_barrier) {
+        const cudaError_t e = cudaMemsetAsync(barrier, 0, sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(tiles);
     cfg.blockDim = dim3(ev::NT);

@@ -55,6 +55,12 @@ struct kaze_handle {
     float* d_k = nullptr;          // contrast factor
     unsigned int* d_hmax = nullptr;
     unsigned int* d_hist = nullptr;
+    // control block: keypoint count, status word, contrast maximum, candidate
+    // count, grid-barrier counter, histogram (+ block counter); one memset
+    // clears it at the start of a whole detection (in_detect)
+    unsigned int* d_ctl = nullptr;
+    size_t ctl_bytes = 0;
+    bool in_detect = false;
     unsigned int* d_count = nullptr;
     unsigned long long* d_cand = nullptr;  // pixels the response launch found above the threshold
     unsigned int* d_cand_count = nullptr;
@@ -244,8 +250,10 @@ kaze_status enqueue_contrast(kaze_handle* h, const float* L0, int pitch, int w, 
         KZ_LAUNCH(h, KK_SET_SCALAR, kz::launch_set_scalar(h->d_k, h->opt.k_override, st));
         return KAZE_OK;
     }
-    KZ_TRY(h, cudaMemsetAsync(h->d_hmax, 0, sizeof(unsigned int), st));
-    KZ_TRY(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned int) * (h->opt.nbins + 1), st));
+    if (!h->in_detect) {  // a whole detection cleared the control block
+        KZ_TRY(h, cudaMemsetAsync(h->d_hmax, 0, sizeof(unsigned int), st));
+        KZ_TRY(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned int) * (h->opt.nbins + 1), st));
+    }
     KZ_LAUNCH(h, KK_GRAD_MAX, kz::launch_grad_max(L0, pitch, w, hh, h->tapsd, h->d_hmax, st, m2_out));
     if (m2_out) {  // histogram and percentile in one launch
         KZ_LAUNCH(h, KK_GRAD_HIST, kz::launch_hist_m2(m2_out, pitch, w, hh, h->d_hmax, h->d_hist, h->opt.nbins,
@@ -265,7 +273,10 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
     cudaStream_t st = h->stream;
     set_geometry(h, w, hh);
     const int P = h->cur_pitch;
-    KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
+    if (h->in_detect)  // count, status, contrast statistics, barrier: one memset
+        KZ_TRY(h, cudaMemsetAsync(h->d_ctl, 0, h->ctl_bytes, st));
+    else
+        KZ_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
     const bool resident = h->N > 1 && !h->surrogate && h->opt.scheme == KAZE_SCHEME_AOS &&
                           h->opt.aos_solver == KAZE_AOS_AUTO && h->d_exchange &&
                           kz::evolve_fits(w, hh, h->tapsd.r, nullptr);
@@ -279,8 +290,10 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
         if (h->opt.k_override > 0.f) {
             KZ_LAUNCH(h, KK_SET_SCALAR, kz::launch_set_scalar(h->d_k, h->opt.k_override, st));
         } else {
-            KZ_TRY(h, cudaMemsetAsync(h->d_hmax, 0, sizeof(unsigned int), st));
-            KZ_TRY(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned int) * h->opt.nbins, st));
+            if (!h->in_detect) {
+                KZ_TRY(h, cudaMemsetAsync(h->d_hmax, 0, sizeof(unsigned int), st));
+                KZ_TRY(h, cudaMemsetAsync(h->d_hist, 0, sizeof(unsigned int) * h->opt.nbins, st));
+            }
             f.hmax_bits = h->d_hmax;
             f.hist = h->d_hist;
             f.nbins = h->opt.nbins;
@@ -289,7 +302,7 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
         KZ_LAUNCH(h, KK_FRONT_EVOLVE,
                   kz::launch_evolve(h->levels, h->cur_plane, P, w, hh, h->N, h->t, h->d_k, h->tapsd,
                                     h->opt.diffusivity, h->d_exchange, h->max_tiles, h->d_barrier, h->d_status, st,
-                                    &f, h->evolve_wait_limit, h->evolve_stall_tile));
+                                    &f, h->evolve_wait_limit, h->evolve_stall_tile, !h->in_detect));
         h->built = true;
         h->responded = false;
         return KAZE_OK;
@@ -312,7 +325,7 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
         KZ_LAUNCH(h, KK_EVOLVE,
                   kz::launch_evolve(h->levels, h->cur_plane, P, w, hh, h->N, h->t, h->d_k, h->tapsd,
                                     h->opt.diffusivity, h->d_exchange, h->max_tiles, h->d_barrier, h->d_status, st,
-                                    nullptr, h->evolve_wait_limit, h->evolve_stall_tile));
+                                    nullptr, h->evolve_wait_limit, h->evolve_stall_tile, !h->in_detect));
         h->built = true;
         h->responded = false;
         return KAZE_OK;
@@ -392,7 +405,7 @@ kz::Candidates candidates(const kaze_handle* h)
 kaze_status enqueue_response(kaze_handle* h)
 {
     const kz::Candidates c = candidates(h);
-    KZ_TRY(h, cudaMemsetAsync(c.count, 0, sizeof(unsigned int), h->stream));
+    if (!h->in_detect) KZ_TRY(h, cudaMemsetAsync(c.count, 0, sizeof(unsigned int), h->stream));
     KZ_LAUNCH_N(h, KK_DOH, kz::doh_launches(h->tab, 0, h->N),
                 kz::launch_doh(h->levels, h->doh, h->cur_pitch, h->cur_plane, h->cur_w, h->cur_h, 0, h->N, h->tab,
                                h->stream, &c));
@@ -407,12 +420,13 @@ kaze_status enqueue_extrema(kaze_handle* h, const float* D, int pitch, long long
                             const kz::LevelTable& tab, bool listed)
 {
     const kz::Candidates c = candidates(h);
-    KZ_TRY(h, cudaMemsetAsync(h->d_count, 0, sizeof(unsigned int), h->stream));
+    if (!h->in_detect) KZ_TRY(h, cudaMemsetAsync(h->d_count, 0, sizeof(unsigned int), h->stream));
     KZ_LAUNCH_N(h, KK_EXTREMA, n >= 3 ? 1 : 0, kz::launch_extrema(D, pitch, plane, w, hh, n, tab, h->opt.dthreshold, h->opt.edge_r, h->d_kp,
                                  h->opt.max_keypoints, h->d_count, h->stream,
                                  listed && D == h->cand_doh ? &c : nullptr));
-    KZ_TRY(h, cudaMemcpyAsync(h->h_count, h->d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
-    KZ_TRY(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    // the count and the status word (adjacent on both sides) in one copy
+    static_assert(sizeof(unsigned int) == sizeof(int), "count and status words");
+    KZ_TRY(h, cudaMemcpyAsync(h->h_count, h->d_count, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
     // the first kp_pre keypoint slots go with the count, so that a detection
     // with no more keypoints than that needs no second round trip to the host
     KZ_TRY(h, cudaMemcpyAsync(h->h_kp_pre, h->d_kp, sizeof(kaze_keypoint) * h->kp_pre, cudaMemcpyDeviceToHost,
@@ -465,9 +479,12 @@ kaze_status run_detect_graph(kaze_handle* h, const float* d_img, int w, int hh, 
     if (h->stream == nullptr || h->stream == cudaStreamLegacy || h->stream == cudaStreamPerThread) {
         // the default streams cannot be captured: launch the same kernels directly
         h->launches = 0;
-        KZ_CHECK(enqueue_build(h, d_img, w, hh, pitch));
-        KZ_CHECK(enqueue_response(h));
-        return enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab, true);
+        h->in_detect = true;
+        kaze_status s = enqueue_build(h, d_img, w, hh, pitch);
+        if (s == KAZE_OK) s = enqueue_response(h);
+        if (s == KAZE_OK) s = enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab, true);
+        h->in_detect = false;
+        return s;
     }
     int slot = -1;
     for (int i = 0; i < 2; ++i) {
@@ -482,9 +499,11 @@ kaze_status run_detect_graph(kaze_handle* h, const float* d_img, int w, int hh, 
         cudaGraph_t graph = nullptr;
         h->launches = 0;
         KZ_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        h->in_detect = true;
         kaze_status s = enqueue_build(h, d_img, w, hh, pitch);
         if (s == KAZE_OK) s = enqueue_response(h);
         if (s == KAZE_OK) s = enqueue_extrema(h, h->doh, h->cur_pitch, h->cur_plane, w, hh, h->N, h->tab, true);
+        h->in_detect = false;
         cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
         if (s != KAZE_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -677,22 +696,21 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     const size_t off_stage = bytes;  bytes += al(sizeof(float) * pm);
     const size_t off_stage2 = bytes; bytes += al(sizeof(float) * pm);
     const size_t off_k = bytes;      bytes += al(sizeof(float));
-    const size_t off_hmax = bytes;   bytes += al(sizeof(unsigned int));
-    const size_t off_hist = bytes;   bytes += al(sizeof(unsigned int) * (o.nbins + 1));  // + a block counter
-    const size_t off_cnt = bytes;    bytes += al(sizeof(unsigned int));
+    // the control block (words): [0] keypoint count, [1] status, [2] contrast
+    // maximum, [3] candidate count, [8] grid barrier, [32 ..] histogram and
+    // its block counter
+    const size_t ctl_bytes = sizeof(unsigned int) * (32 + (size_t)o.nbins + 1);
+    const size_t off_ctl = bytes;    bytes += al(ctl_bytes);
     // candidates of the extremum test: a sixteenth of the pixels of all
     // levels (more falls back to the full scan)
     const unsigned cand_cap = (unsigned)std::min<size_t>(std::max<size_t>((size_t)N * pm / 16, 65536), 1u << 30);
     const size_t off_cand = bytes;   bytes += al(sizeof(unsigned long long) * cand_cap);
-    const size_t off_ccnt = bytes;   bytes += al(sizeof(unsigned int));
-    const size_t off_status = bytes; bytes += al(sizeof(int));
     const size_t off_kp = bytes;     bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
     const size_t off_dkp = bytes;    bytes += al(sizeof(kaze_keypoint) * (size_t)o.max_keypoints);
     const size_t off_desc = bytes;   bytes += al(sizeof(float) * 64 * (size_t)o.max_keypoints);
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t off_xchg = bytes;   bytes += al(sizeof(float) * kz::evolve_exchange_floats(sms));
-    const size_t off_bar = bytes;    bytes += al(sizeof(unsigned int));
     cudaError_t e = cudaMalloc(&h->arena, bytes);
     if (e != cudaSuccess) {
         delete h;
@@ -707,18 +725,20 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     h->staging = (float*)(a + off_stage);
     h->staging2 = (float*)(a + off_stage2);
     h->d_k = (float*)(a + off_k);
-    h->d_hmax = (unsigned int*)(a + off_hmax);
-    h->d_hist = (unsigned int*)(a + off_hist);
-    h->d_count = (unsigned int*)(a + off_cnt);
+    h->d_ctl = (unsigned int*)(a + off_ctl);
+    h->ctl_bytes = ctl_bytes;
+    h->d_count = h->d_ctl;
+    h->d_status = (int*)(h->d_ctl + 1);
+    h->d_hmax = h->d_ctl + 2;
+    h->d_cand_count = h->d_ctl + 3;
+    h->d_barrier = h->d_ctl + 8;
+    h->d_hist = h->d_ctl + 32;
     h->d_cand = (unsigned long long*)(a + off_cand);
-    h->d_cand_count = (unsigned int*)(a + off_ccnt);
     h->cand_cap = cand_cap;
-    h->d_status = (int*)(a + off_status);
     h->d_kp = (kaze_keypoint*)(a + off_kp);
     h->d_dkp = (kaze_keypoint*)(a + off_dkp);
     h->d_desc = (float*)(a + off_desc);
     h->d_exchange = sms > 0 ? (float*)(a + off_xchg) : nullptr;
-    h->d_barrier = (unsigned int*)(a + off_bar);
     h->max_tiles = sms;
     e = cudaMallocHost(&h->h_count, 2 * sizeof(unsigned int));
     if (e != cudaSuccess) {

@@ -195,7 +195,8 @@ size_t aos_cols_smem_bytes(int h);
 // (k_evolve.cu).  evolve_fits: whether a w x h image with a gradient
 // smoothing radius `radius` can take it on the current device (tiles one per
 // SM); `exchange` holds evolve_exchange_floats(max_tiles) floats, `barrier`
-// one counter; a timed-out grid barrier sets bit 0 of *status.  wait_limit:
+// one counter (zeroed by the launch unless zero_barrier is false: the
+// caller did); a timed-out grid barrier sets bit 0 of *status.  wait_limit:
 // SM cycles a barrier wait may take (0: 2^31); stall_tile >= 0 (a test
 // hook) makes that tile never arrive, so every wait runs out.
 // The front of the pipeline inside the same launch: with `img`, level 0 is
@@ -251,7 +252,7 @@ bool evolve_front_fits(int r0, int nbins);
 cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int h, int n_levels, const double* t,
                           float* d_k, const GaussTaps& taps, int diffusivity, float* exchange, int max_tiles,
                           unsigned int* barrier, int* status, cudaStream_t st, const EvolveFront* front = nullptr,
-                          long long wait_limit = 0, int stall_tile = -1);
+                          long long wait_limit = 0, int stall_tile = -1, bool zero_barrier = true);
 
 // The pixels the extremum test of Sec. III-2 can accept: response above the
 // threshold, on a level in [lo, hi] (1 .. N-2), one pixel or more inside the
