@@ -351,9 +351,10 @@ def run_reference(args, rank, world):
         rates.append(r)
         secs += dt
     value = args.steps * cw * ch / secs / 1e6
-    sample = (f"centred {cw}x{ch} crop of the 1920x1200 workload image per step, "
-              f"{OCTAVES}x{SUBLEVELS} levels, scale space + response + extrema, FP64 oracle on "
-              f"{cores} host threads")
+    part = ("the whole 1920x1200 workload image" if (cw, ch) == (W_IMG, H_IMG)
+            else f"centred {cw}x{ch} crop of the 1920x1200 workload image")
+    sample = (f"{part} per step, {OCTAVES}x{SUBLEVELS} levels, scale space + response + extrema, "
+              f"FP64 oracle on {cores} host threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
