@@ -60,9 +60,14 @@ struct kaze_batch {
     void* d_resident = nullptr;      // exchange buffers, barrier counters, candidate list
     std::vector<float*> exchange;    // per image
     unsigned* d_ebar = nullptr;      // per image barrier counter
-    unsigned long long* d_cand = nullptr;
-    unsigned* d_cand_count = nullptr;
+    // the images' response and extrema launches run on kResBranches graph
+    // branches, each with its own candidate list
+    static constexpr int kResBranches = 4;
+    unsigned long long* d_cand = nullptr;  // kResBranches lists of cand_cap entries
+    unsigned* d_cand_count = nullptr;      // kResBranches counters
     unsigned cand_cap = 0;
+    cudaStream_t res_s[kResBranches] = {};
+    cudaEvent_t res_ev[kResBranches + 1] = {};  // [0] fork, [1..] joins
     size_t eparams_bytes = 0;
     void* d_eparams = nullptr;       // per image launch parameters
     void* h_eparams = nullptr;       // pinned copy, refreshed with the input pointers
@@ -320,9 +325,9 @@ kaze_status prepare_resident(kaze_batch* b)
         bytes += al(sizeof(unsigned) * b->n);
         b->cand_cap = (unsigned)std::min<size_t>(std::max<size_t>((size_t)b->N * max_plane / 16, 65536), 1u << 30);
         const size_t off_cand = bytes;
-        bytes += al(sizeof(unsigned long long) * b->cand_cap);
+        bytes += al(sizeof(unsigned long long) * b->cand_cap) * kaze_batch::kResBranches;
         const size_t off_ccnt = bytes;
-        bytes += al(sizeof(unsigned));
+        bytes += al(sizeof(unsigned) * kaze_batch::kResBranches);
         b->eparams_bytes = (kz::evolve_params_bytes() + 15) / 16 * 16;
         const size_t off_par = bytes;
         bytes += al(b->eparams_bytes * b->n);
@@ -335,6 +340,10 @@ kaze_status prepare_resident(kaze_batch* b)
         b->d_cand = (unsigned long long*)(a + off_cand);
         b->d_cand_count = (unsigned*)(a + off_ccnt);
         b->d_eparams = a + off_par;
+        for (int k = 0; k < kaze_batch::kResBranches; ++k)
+            KB_TRY(b, cudaStreamCreateWithFlags(&b->res_s[k], cudaStreamNonBlocking));
+        for (int k = 0; k <= kaze_batch::kResBranches; ++k)
+            KB_TRY(b, cudaEventCreateWithFlags(&b->res_ev[k], cudaEventDisableTiming));
     }
     return refresh_resident(b);
 }
@@ -348,19 +357,31 @@ kaze_status enqueue_resident(kaze_batch* b)
     KB_TRY(b, cudaMemsetAsync(b->d_ebar, 0, sizeof(unsigned) * b->n, st));
     KB_TRY(b, cudaMemcpyAsync(b->d_eparams, b->h_eparams, b->eparams_bytes * b->n, cudaMemcpyHostToDevice, st));
     KB_TRY(b, kz::launch_evolve_batch(b->d_eparams, b->d_work, b->d_off, b->egrid, st));
-    kz::Candidates c;
-    c.list = b->d_cand;
-    c.count = b->d_cand_count;
-    c.cap = b->cand_cap;
-    c.thr = b->opt.dthreshold;
-    c.lo = 1;
-    c.hi = b->N - 2;
+    // each image's response and extrema on branch i % kResBranches, so that
+    // the small images' launches run side by side
+    constexpr int NB = kaze_batch::kResBranches;
+    KB_TRY(b, cudaEventRecord(b->res_ev[0], st));
+    for (int k = 0; k < NB; ++k) KB_TRY(b, cudaStreamWaitEvent(b->res_s[k], b->res_ev[0], 0));
+    const size_t list_stride = (sizeof(unsigned long long) * b->cand_cap + 255) / 256 * 256 / sizeof(unsigned long long);
     for (int i = 0; i < b->n; ++i) {
         const ImageDesc& d = b->h_desc[i];
-        KB_TRY(b, cudaMemsetAsync(c.count, 0, sizeof(unsigned), st));
-        KB_TRY(b, kz::launch_doh(d.levels, d.doh, d.pitch, d.plane, d.w, d.h, 0, b->N, P.tab, st, &c));
+        const int k = i % NB;
+        cudaStream_t sk = b->res_s[k];
+        kz::Candidates c;
+        c.list = b->d_cand + list_stride * k;
+        c.count = b->d_cand_count + k;
+        c.cap = b->cand_cap;
+        c.thr = b->opt.dthreshold;
+        c.lo = 1;
+        c.hi = b->N - 2;
+        KB_TRY(b, cudaMemsetAsync(c.count, 0, sizeof(unsigned), sk));
+        KB_TRY(b, kz::launch_doh(d.levels, d.doh, d.pitch, d.plane, d.w, d.h, 0, b->N, P.tab, sk, &c));
         KB_TRY(b, kz::launch_extrema(d.doh, d.pitch, d.plane, d.w, d.h, b->N, P.tab, b->opt.dthreshold,
-                                     b->opt.edge_r, d.kp, d.kp_cap, d.kp_count, st, &c));
+                                     b->opt.edge_r, d.kp, d.kp_cap, d.kp_count, sk, &c));
+    }
+    for (int k = 0; k < NB; ++k) {
+        KB_TRY(b, cudaEventRecord(b->res_ev[1 + k], b->res_s[k]));
+        KB_TRY(b, cudaStreamWaitEvent(st, b->res_ev[1 + k], 0));
     }
     KB_TRY(b, cudaMemcpyAsync(b->h_count_status, b->d_count_status, sizeof(unsigned) * (b->n + 1),
                               cudaMemcpyDeviceToHost, st));
@@ -807,6 +828,10 @@ KAZE_API void kaze_batch_destroy(kaze_batch* b)
     if (b->d_work) cudaFree(b->d_work);
     if (b->d_off) cudaFree(b->d_off);
     if (b->d_resident) cudaFree(b->d_resident);
+    for (auto sres : b->res_s)
+        if (sres) cudaStreamDestroy(sres);
+    for (auto e : b->res_ev)
+        if (e) cudaEventDestroy(e);
     if (b->h_eparams) cudaFreeHost(b->h_eparams);
     if (b->arena) cudaFree(b->arena);
     if (b->h_desc) cudaFreeHost(b->h_desc);
