@@ -170,3 +170,21 @@ def test_handle_build_batch_equals_batch_object(kz):
     with kz.Kaze(256, 256, scheme=kz.SCHEME_FED) as k:
         with pytest.raises(kz.KazeError):
             k.build_batch(xs)
+
+
+def test_resident_mode_needs_every_image_to_fit(kz):
+    """A batch with an image of more tiles than SMs (4096x3072: 32 x 26 tiles
+    of 128 x 120) starts in the work-queue execution, refuses the resident
+    one (and keeps its tuning), and detects; a batch of small images starts
+    resident."""
+    sizes = [(4096, 3072), (640, 480)]
+    xs = [torch.rand(h, w, device="cuda") for w, h in sizes]
+    with kz.Batch(sizes, octaves=1, sublevels=3) as b:
+        assert b.tuning()[0] == kz.BATCH_PERSISTENT
+        with pytest.raises(kz.KazeError):
+            b.set_tuning(kz.BATCH_RESIDENT, 4, 1, 8)
+        assert b.tuning()[0] == kz.BATCH_PERSISTENT
+        kps = b.detect(xs)
+        assert len(kps) == 2
+    with kz.Batch(SIZES, octaves=1, sublevels=3) as b:
+        assert b.tuning()[0] == kz.BATCH_RESIDENT
