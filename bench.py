@@ -137,12 +137,15 @@ def algorithmic_bytes(kind, pixels, n_levels, nbins=300):
     half (write u_x: 4 P); the column half is pass B (16 P); the resident
     evolution takes all N - 1 steps in one launch (28 P each), and with the
     presmoothing and the contrast factor inside it (front_evolve) also their
-    8 P + 8 P."""
+    8 P + 8 P.  The streamed tile passes are pass A (stream_a, 12 P a step)
+    and pass B (stream_b, 16 P), the line pass between them (stream_x)
+    moving only the segment records."""
     steps = n_levels - 1
     table = {
         "presmooth": 8, "grad_max": 4, "grad_hist": 4, "conductance": 8 * steps,
         "aos_rows": 4 * steps, "aos_cols": 16 * steps, "aos_evolve": 28 * steps,
         "front_evolve": 8 + 8 + 28 * steps,
+        "stream_a": 12 * steps, "stream_b": 16 * steps,
         "doh": 8 * n_levels, "extrema": 4 * n_levels,
     }
     if kind in table:
@@ -195,6 +198,7 @@ KIND_SOURCES = {
     "aos_cols": ["aos_solver.cuh", "k_aos.cu", "k_aos_va.cu", "k_aos_vb.cu", "k_aos_vc.cu", "k_aos_vd.cu"],
     "aos_evolve": ["k_evolve.cu"],
     "front_evolve": ["k_evolve.cu"],
+    "stream_a": ["k_evolve.cu"], "stream_x": ["k_evolve.cu"], "stream_b": ["k_evolve.cu"],
     "doh": ["k_detector.cu", "doh_walk.cuh"], "extrema": ["k_detector.cu"], "describe": ["k_describe.cu"],
     "fed": ["k_fed.cu"],
 }

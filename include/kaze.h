@@ -82,6 +82,14 @@ typedef enum {
 #define KAZE_AOS_LINES 1  /* always the line kernels: per step a conductance
                              pass, then every row and every column solved by
                              one CTA strip each (no cooperative launch)         */
+#define KAZE_AOS_STREAMED 2 /* the streamed tile passes where they fit (at most
+                             64 tiles along a line; the line kernels beyond):
+                             per step three launches over all tiles
+                             (conductance and chunk records of every tile;
+                             every segment's outside neighbours from its line;
+                             the re-solves, L_i written once), the resident
+                             evolution's tile arithmetic without its residency
+                             (slower than the line kernels on large images)   */
 
 /* Normalisation of the Hessian determinant, Eq. 8. */
 #define KAZE_DOH_SIGMA4 0         /* s_i^4 det, s_i = max(1, round(sigma_i)) (default) */
@@ -103,7 +111,7 @@ typedef struct kaze_options {
     int scheme;           /* KAZE_SCHEME_AOS (default) or KAZE_SCHEME_FED         */
     float fed_tau_max;    /* FED stability limit, (0, 0.25] (0.25)                */
     int extrema_window;   /* KAZE_EXTREMA_3X3 (default) or _SIGMA_WINDOW          */
-    int aos_solver;       /* KAZE_AOS_AUTO (default) or KAZE_AOS_LINES            */
+    int aos_solver;       /* KAZE_AOS_AUTO (default), _LINES or _STREAMED           */
 } kaze_options;
 
 /* One detected keypoint (Sec. II-B). */

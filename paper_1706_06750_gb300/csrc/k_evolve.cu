@@ -751,6 +751,108 @@ __device__ __forceinline__ void store_rec(float* d, int st, const Rec& R)
     d[5 * st] = R.WL;
 }
 
+// ------------------------------------------------ the phases of a tile's step
+// (shared by the resident launch and the streamed passes)
+
+// 2. Every line of the tile cut into chunks, each chunk's spike record into
+// RRc (rows, [k][f][r]) and CRc (columns, [k][f][c]); warp jobs of 32 lines
+// and one chunk.
+__device__ __forceinline__ void chunk_records(const float* __restrict__ LH, const float* __restrict__ G,
+                                              float* __restrict__ RRc, float* __restrict__ CRc, int tw, int th,
+                                              float tau)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int job = warp; job < 4 * KR + 4 * KC; job += NWARP) {
+        if (job < 4 * KR) {
+            const int r = (job / KR) * 32 + lane, k = job % KR;
+            if (r < th) {
+                const Chunk<MR> ch{LH + (r + HALO) * LS + (k * MR + HALO), G + (r + 1) * GS + (k * MR + 1), 1, 1,
+                                   tau};
+                store_rec(RRc + (k * REC) * TH + r, TH, ch.record());
+            }
+        } else {
+            const int jb = job - 4 * KR;
+            const int c = (jb / KC) * 32 + lane, k = jb % KC;
+            if (c < tw) {
+                const Chunk<MC> ch{LH + (k * MC + HALO) * LS + (c + HALO), G + (k * MC + 1) * GS + (c + 1), LS, GS,
+                                   tau};
+                store_rec(CRc + (k * REC) * TW + c, TW, ch.record());
+            }
+        }
+    }
+}
+
+// 3. The segment record of the thread's line (row li, or column li) from its
+// 8 chunk records; the joints of the merges go to P, Q.
+__device__ __forceinline__ Rec segment_record(const float* __restrict__ RRc, const float* __restrict__ CRc,
+                                              bool row_line, int li, Pt (&P)[8], Pt (&Q)[8])
+{
+    const float* src = row_line ? RRc + li : CRc + li;
+    const int st = row_line ? TH : TW;
+    Rec S = load_rec(src, st);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) S = merge(S, load_rec(src + k * REC * st, st), P[k], Q[k]);
+    return S;
+}
+
+// Every chunk's external neighbours from the segment's (xl, xr), walking the
+// joints back from the segment's right end, into XR / XC ([k][2][line]).
+__device__ __forceinline__ void chunk_externals(float* __restrict__ XR, float* __restrict__ XC, bool row_line, int li,
+                                                const Pt (&P)[8], const Pt (&Q)[8], float xl, float xr)
+{
+    float* xe = row_line ? XR + li : XC + li;
+    const int st = row_line ? TH : TW;
+    float right = xr;
+#pragma unroll
+    for (int k = 7; k >= 1; --k) {
+        const float first_k = eval(Q[k], xl, right);
+        xe[(k * 2 + 0) * st] = eval(P[k], xl, right);
+        xe[(k * 2 + 1) * st] = right;
+        right = first_k;
+    }
+    xe[0] = xl;
+    xe[st] = right;
+}
+
+// 5. The chunks solved again with their external terms on the right-hand
+// side: rows give u_x (U), columns u_y and L = (u_x + u_y) / 2, into the tile
+// and the level plane.
+__device__ __forceinline__ void resolve_tile(float* __restrict__ LH, const float* __restrict__ G, float* __restrict__ U,
+                                             const float* __restrict__ XR, const float* __restrict__ XC,
+                                             float* __restrict__ Lout, int pitch, int x0, int y0, int tw, int th,
+                                             float tau)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int job = warp; job < 4 * KR; job += NWARP) {
+        const int r = (job / KR) * 32 + lane, k = job % KR;
+        if (r < th) {
+            const Chunk<MR> ch{LH + (r + HALO) * LS + (k * MR + HALO), G + (r + 1) * GS + (k * MR + 1), 1, 1, tau};
+            float x[MR];
+            ch.solve(XR[(k * 2 + 0) * TH + r], XR[(k * 2 + 1) * TH + r], x);
+            float* u = U + r * US + k * MR;
+#pragma unroll
+            for (int i = 0; i < MR; ++i) u[i] = x[i];
+        }
+    }
+    __syncthreads();
+    for (int job = warp; job < 4 * KC; job += NWARP) {
+        const int c = (job / KC) * 32 + lane, k = job % KC;
+        if (c < tw) {
+            const Chunk<MC> ch{LH + (k * MC + HALO) * LS + (c + HALO), G + (k * MC + 1) * GS + (c + 1), LS, GS,
+                               tau};
+            float x[MC];
+            ch.solve(XC[(k * 2 + 0) * TW + c], XC[(k * 2 + 1) * TW + c], x);
+#pragma unroll
+            for (int i = 0; i < MC; ++i) {
+                const int r = k * MC + i;
+                const float v = 0.5f * (U[r * US + c] + x[i]);
+                LH[(r + HALO) * LS + (c + HALO)] = v;
+                if (r < th) Lout[(size_t)(y0 + r) * pitch + (x0 + c)] = v;
+            }
+        }
+    }
+}
+
 // Shared state of a tile's run besides the tile arrays.
 struct TileShared {
     int abort;
@@ -889,38 +991,17 @@ __device__ __forceinline__ bool evolve_tile(const Params& p, int tile, TileShare
         __syncthreads();
 
         // 2. chunk records (warp jobs: 32 lines x one chunk)
-        for (int job = warp; job < 4 * KR + 4 * KC; job += NWARP) {
-            if (job < 4 * KR) {
-                const int r = (job / KR) * 32 + lane, k = job % KR;
-                if (r < th) {
-                    const Chunk<MR> ch{LH + (r + HALO) * LS + (k * MR + HALO), G + (r + 1) * GS + (k * MR + 1), 1,
-                                       1, tau};
-                    store_rec(RRc + (k * REC) * TH + r, TH, ch.record());
-                }
-            } else {
-                const int jb = job - 4 * KR;
-                const int c = (jb / KC) * 32 + lane, k = jb % KC;
-                if (c < tw) {
-                    const Chunk<MC> ch{LH + (k * MC + HALO) * LS + (c + HALO), G + (k * MC + 1) * GS + (c + 1), LS,
-                                       GS, tau};
-                    store_rec(CRc + (k * REC) * TW + c, TW, ch.record());
-                }
-            }
-        }
+        chunk_records(LH, G, RRc, CRc, tw, th, tau);
         __syncthreads();
 
         // 3. segment records (one thread per line) to global memory; the
         // joints of the chunk merges stay in registers for step 4
         Pt P[8], Q[8];
         if (row_line || col_line) {
-            const float* src = row_line ? RRc + li : CRc + li;
-            const int st = row_line ? TH : TW;
-            Rec S = load_rec(src, st);
-#pragma unroll
-            for (int k = 1; k < 8; ++k) S = merge(S, load_rec(src + k * REC * st, st), P[k], Q[k]);
+            const Rec seg = segment_record(RRc, CRc, row_line, li, P, Q);
             float* dst = row_line ? p.xrow + ((size_t)(y0 + li) * p.tiles_x + tx) * REC
                                   : p.xcol + ((size_t)(x0 + li) * p.tiles_y + ty) * REC;
-            store_rec(dst, 1, S);
+            store_rec(dst, 1, seg);
         }
         nbar += ntiles;
         if (!grid_barrier(p, tile, nbar, &S.abort)) return false;
@@ -973,53 +1054,12 @@ __device__ __forceinline__ bool evolve_tile(const Params& p, int tile, TileShare
         __syncthreads();  // the staged records are dead: XE is written next
         // every chunk's external neighbours, walking the chunk joints back
         // from the segment's right end
-        if (row_line || col_line) {
-            float* xe = row_line ? XR + li : XC + li;
-            const int st = row_line ? TH : TW;
-            float right = xr;
-#pragma unroll
-            for (int k = 7; k >= 1; --k) {
-                const float first_k = eval(Q[k], xl, right);
-                xe[(k * 2 + 0) * st] = eval(P[k], xl, right);
-                xe[(k * 2 + 1) * st] = right;
-                right = first_k;
-            }
-            xe[0] = xl;
-            xe[st] = right;
-        }
+        if (row_line || col_line) chunk_externals(XR, XC, row_line, li, P, Q, xl, xr);
         __syncthreads();
 
-        // 5a. row chunks with their externals: u_x into SC
-        float* U = SC;
-        for (int job = warp; job < 4 * KR; job += NWARP) {
-            const int r = (job / KR) * 32 + lane, k = job % KR;
-            if (r < th) {
-                const Chunk<MR> ch{LH + (r + HALO) * LS + (k * MR + HALO), G + (r + 1) * GS + (k * MR + 1), 1, 1, tau};
-                float x[MR];
-                ch.solve(XR[(k * 2 + 0) * TH + r], XR[(k * 2 + 1) * TH + r], x);
-                float* u = U + r * US + k * MR;
-#pragma unroll
-                for (int i = 0; i < MR; ++i) u[i] = x[i];
-            }
-        }
-        __syncthreads();
-        // 5b. column chunks: L = (u_x + u_y) / 2 into the tile and the level plane
-        for (int job = warp; job < 4 * KC; job += NWARP) {
-            const int c = (job / KC) * 32 + lane, k = job % KC;
-            if (c < tw) {
-                const Chunk<MC> ch{LH + (k * MC + HALO) * LS + (c + HALO), G + (k * MC + 1) * GS + (c + 1), LS, GS,
-                                   tau};
-                float x[MC];
-                ch.solve(XC[(k * 2 + 0) * TW + c], XC[(k * 2 + 1) * TW + c], x);
-#pragma unroll
-                for (int i = 0; i < MC; ++i) {
-                    const int r = k * MC + i;
-                    const float v = 0.5f * (U[r * US + c] + x[i]);
-                    LH[(r + HALO) * LS + (c + HALO)] = v;
-                    if (r < th) Lout[(size_t)(y0 + r) * p.pitch + (x0 + c)] = v;
-                }
-            }
-        }
+        // 5. rows: u_x into SC; columns: L = (u_x + u_y) / 2 into the tile and
+        // the level plane
+        resolve_tile(LH, G, SC, XR, XC, Lout, p.pitch, x0, y0, tw, th, tau);
         if (lev + 1 < p.n_levels) {
             // 6. every tile's L_lev is in the level plane: read the ring
             nbar += ntiles;
@@ -1066,11 +1106,167 @@ k_evolve_batch(const Params* __restrict__ ps, const int2* __restrict__ work, con
     }
 }
 
+// ------------------------------------------------------- the streamed form
+// Images whose tiles exceed one per SM take each AOS step in three launches
+// over all tiles, the tiles streaming through the SMs:
+//   A: the tile of L_{lev-1} with its ring from the level plane, g on the
+//      tile and its ring (ghosts past the image) -- the tile's own g to the
+//      conductance plane --, the chunk and segment records to global memory;
+//   X: one thread per line merges the records of the line's segments (prefix
+//      from the left, suffix from the right) and solves every segment's two
+//      outside neighbours;
+//   B: the tile's L and g (own pixels and ring from the planes, ghosts past
+//      the image), the chunk records again (for the joints), the chunk
+//      externals from the segment's neighbours, the re-solves, L_lev to the
+//      level plane.
+// The arithmetic is the resident launch's, the launch boundaries replacing
+// its grid barriers.
+
+__global__ void __launch_bounds__(NT, 1) k_stream_a(const __grid_constant__ Params p, int lev, float* __restrict__ gpl)
+{
+    extern __shared__ __align__(16) float sm[];
+    float* LH = sm + OFF_L;
+    float* SC = sm + OFF_A;
+    float* G = sm + OFF_B;
+    float* RRc = SC;
+    float* CRc = SC + RREC;
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int tw = min(TW, p.w - x0), th = min(TH, p.h - y0);
+    const bool row_line = tid < th;
+    const bool col_line = tid >= 128 && tid - 128 < tw;
+    const int li = row_line ? tid : tid - 128;
+    const float tau = p.tau[lev];
+    const float kk = *p.d_k;
+    const float inv_k2 = 1.f / (kk * kk);
+    load_all(LH, p.levels + (size_t)(lev - 1) * p.plane, p, x0, y0);
+    __syncthreads();
+    h_pass(LH, G, p);
+    __syncthreads();
+    v_pass(G, SC, p);
+    __syncthreads();
+    if (p.diffusivity == KAZE_G1)
+        scharr_pass<MODE_G1>(SC, G, inv_k2, x0, y0, tw, th, p.w, p.h);
+    else
+        scharr_pass<MODE_G2>(SC, G, inv_k2, x0, y0, tw, th, p.w, p.h);
+    __syncthreads();
+    // the tile's own g to the plane (pass B reads its ring from the neighbours')
+    for (int e = tid; e < th * tw; e += NT) {
+        const int r = e / tw, c = e - r * tw;
+        gpl[(size_t)(y0 + r) * p.pitch + (x0 + c)] = G[(r + 1) * GS + (c + 1)];
+    }
+    ghost_conductance(G, x0, y0, p.w, p.h);
+    __syncthreads();
+    chunk_records(LH, G, RRc, CRc, tw, th, tau);
+    __syncthreads();
+    if (row_line || col_line) {
+        Pt P[8], Q[8];
+        const Rec seg = segment_record(RRc, CRc, row_line, li, P, Q);
+        float* dst = row_line ? p.xrow + ((size_t)(y0 + li) * p.tiles_x + tx) * REC
+                              : p.xcol + ((size_t)(x0 + li) * p.tiles_y + ty) * REC;
+        store_rec(dst, 1, seg);
+    }
+}
+
+constexpr int STREAM_TMAX = 64;  // segments of a line the line pass takes
+
+// One thread per line (rows 0..h-1, then columns 0..w-1): the outside
+// neighbours (xl, xr) of every segment of the line, to ext[line][t][2].
+__global__ void __launch_bounds__(128) k_stream_x(const __grid_constant__ Params p, float* __restrict__ erow,
+                                                  float* __restrict__ ecol)
+{
+    const int line = blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= p.h + p.w) return;
+    const bool row = line < p.h;
+    const int li = row ? line : line - p.h;
+    const int T = row ? p.tiles_x : p.tiles_y;
+    const float* rec = row ? p.xrow + (size_t)li * T * REC : p.xcol + (size_t)li * T * REC;
+    float* ext = row ? erow + (size_t)li * T * 2 : ecol + (size_t)li * T * 2;
+    // prefix records: pre[t] = the union of segments 0 .. t - 1
+    Rec pre[STREAM_TMAX];
+    if (T > 1) pre[1] = load_rec(rec, 1);
+    for (int t = 2; t < T; ++t) pre[t] = merge(pre[t - 1], load_rec(rec + (t - 1) * REC, 1));
+    // from the right: suf = the union of segments t + 1 .. T - 1
+    Rec suf{};
+    for (int t = T - 1; t >= 0; --t) {
+        const Rec own = load_rec(rec + t * REC, 1);
+        Pt P1{0.f, 0.f, 0.f}, Q1;
+        Rec Mx = own;
+        if (t > 0) Mx = merge(pre[t], own, P1, Q1);
+        float xl = 0.f, xr = 0.f;
+        if (t + 1 < T) {
+            Pt P2, Q2;
+            merge(Mx, suf, P2, Q2);
+            xr = Q2.y;
+        }
+        if (t > 0) xl = P1.y - P1.W * xr;
+        ext[t * 2 + 0] = xl;
+        ext[t * 2 + 1] = xr;
+        suf = t + 1 < T ? merge(own, suf) : own;
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_stream_b(const __grid_constant__ Params p, int lev,
+                                                    const float* __restrict__ gpl, const float* __restrict__ erow,
+                                                    const float* __restrict__ ecol)
+{
+    extern __shared__ __align__(16) float sm[];
+    float* LH = sm + OFF_L;
+    float* SC = sm + OFF_A;
+    float* XE = sm + OFF_X;
+    float* G = sm + OFF_B;
+    float* RRc = SC;
+    float* CRc = SC + RREC;
+    float* XR = XE;
+    float* XC = XE + KR * 2 * TH;
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int tw = min(TW, p.w - x0), th = min(TH, p.h - y0);
+    const bool row_line = tid < th;
+    const bool col_line = tid >= 128 && tid - 128 < tw;
+    const int li = row_line ? tid : tid - 128;
+    const float tau = p.tau[lev];
+    const float* Lp = p.levels + (size_t)(lev - 1) * p.plane;
+    // the tile's L with its ring (the chunk solves read the tile's own pixels;
+    // a ragged tile's elements past the image must hold finite values: the
+    // reflected ones) and g on the tile and its ring inside the image,
+    // ghosts past it
+    load_all(LH, Lp, p, x0, y0);
+    for (int e = tid; e < (th + 2) * (tw + 2); e += NT) {
+        const int r = e / (tw + 2) - 1, c = e - (r + 1) * (tw + 2) - 1;
+        const int y = y0 + r, x = x0 + c;
+        if (y >= 0 && y < p.h && x >= 0 && x < p.w) G[(r + 1) * GS + (c + 1)] = __ldcg(gpl + (size_t)y * p.pitch + x);
+    }
+    __syncthreads();
+    ghost_conductance(G, x0, y0, p.w, p.h);
+    __syncthreads();
+    chunk_records(LH, G, RRc, CRc, tw, th, tau);
+    __syncthreads();
+    Pt P[8], Q[8];
+    if (row_line || col_line) {
+        segment_record(RRc, CRc, row_line, li, P, Q);
+        const float* e = row_line ? erow + ((size_t)(y0 + li) * p.tiles_x + tx) * 2
+                                  : ecol + ((size_t)(x0 + li) * p.tiles_y + ty) * 2;
+        chunk_externals(XR, XC, row_line, li, P, Q, __ldcg(e), __ldcg(e + 1));
+    }
+    __syncthreads();
+    resolve_tile(LH, G, SC, XR, XC, p.levels + (size_t)lev * p.plane, p.pitch, x0, y0, tw, th, tau);
+}
+
 }  // namespace ev
 
 cudaError_t configure_evolve_kernel()
 {
-    return cudaFuncSetAttribute(ev::k_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ev::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(ev::k_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ev::SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ev::k_stream_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ev::SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ev::k_stream_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ev::SMEM_BYTES);
+    return e;
 }
 
 bool evolve_front_fits(int r0, int nbins) { return r0 == ev::R0MAX && nbins * ev::NWARP <= ev::A_SIZE; }
@@ -1178,6 +1374,47 @@ cudaError_t launch_evolve(float* levels, long long plane, int pitch, int w, int 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, ev::k_evolve, p);
+}
+
+size_t evolve_stream_floats(int max_w, int max_h)
+{
+    const size_t tx = (size_t)(max_w + ev::TW - 1) / ev::TW, ty = (size_t)(max_h + ev::TH - 1) / ev::TH;
+    auto r4 = [](size_t n) { return (n + 3) & ~(size_t)3; };
+    return r4(max_h * tx * ev::REC) + r4(max_w * ty * ev::REC) + r4(max_h * tx * 2) + r4(max_w * ty * 2) + 64;
+}
+
+bool evolve_stream_fits(int w, int h, int radius)
+{
+    if (radius < 1 || radius > ev::RMAX || w < 1 || h < 1) return false;
+    const int tx = (w + ev::TW - 1) / ev::TW, ty = (h + ev::TH - 1) / ev::TH;
+    return tx <= ev::STREAM_TMAX && ty <= ev::STREAM_TMAX;
+}
+
+cudaError_t launch_stream_pass(int pass, int lev, float* levels, long long plane, int pitch, int w, int h,
+                               int n_levels, const double* t, float* d_k, const GaussTaps& taps, int diffusivity,
+                               float* g, float* scratch, cudaStream_t st)
+{
+    if (!evolve_stream_fits(w, h, taps.r) || lev < 1 || lev >= n_levels || !scratch || !g)
+        return cudaErrorInvalidValue;
+    const int tx = (w + ev::TW - 1) / ev::TW, ty = (h + ev::TH - 1) / ev::TH;
+    auto r4 = [](size_t n) { return (n + 3) & ~(size_t)3; };
+    float* xrow = scratch;
+    float* xcol = xrow + r4((size_t)h * tx * ev::REC);
+    float* erow = xcol + r4((size_t)w * ty * ev::REC);
+    float* ecol = erow + r4((size_t)h * tx * 2);
+    ev::Params p;
+    if (!make_params(p, levels, plane, pitch, w, h, n_levels, t, d_k, taps, diffusivity, scratch, nullptr, nullptr,
+                     nullptr, 0, -1, 0.f))
+        return cudaErrorInvalidValue;
+    p.xrow = xrow;
+    p.xcol = xcol;
+    if (pass == 0)
+        ev::k_stream_a<<<tx * ty, ev::NT, ev::SMEM_BYTES, st>>>(p, lev, g);
+    else if (pass == 1)
+        ev::k_stream_x<<<(h + w + 127) / 128, 128, 0, st>>>(p, erow, ecol);
+    else
+        ev::k_stream_b<<<tx * ty, ev::NT, ev::SMEM_BYTES, st>>>(p, lev, g, erow, ecol);
+    return cudaGetLastError();
 }
 
 size_t evolve_params_bytes() { return sizeof(ev::Params); }

@@ -26,12 +26,12 @@ namespace {
 enum KernelKind {
     KK_PRESMOOTH = 0, KK_GRAD_MAX, KK_GRAD_HIST, KK_PERCENTILE, KK_SET_SCALAR,
     KK_CONDUCTANCE, KK_AOS_ROWS, KK_AOS_COLS, KK_DOH, KK_EXTREMA, KK_SURROGATE, KK_DESCRIBE, KK_FED, KK_EVOLVE,
-    KK_FRONT_EVOLVE, KK_COUNT
+    KK_FRONT_EVOLVE, KK_STREAM_A, KK_STREAM_X, KK_STREAM_B, KK_COUNT
 };
 const char* const kKindNames[KK_COUNT] = {
     "presmooth", "grad_max", "grad_hist", "percentile", "set_scalar",
     "conductance", "aos_rows", "aos_cols", "doh", "extrema", "surrogate", "describe", "fed", "aos_evolve",
-    "front_evolve"};
+    "front_evolve", "stream_a", "stream_x", "stream_b"};
 }  // namespace
 
 struct kaze_handle {
@@ -68,6 +68,7 @@ struct kaze_handle {
     const float* cand_doh = nullptr;  // the response stack the list was made from
     int* d_status = nullptr;         // bit 0: a bounded device wait ran out
     float* d_exchange = nullptr;     // segment records of the resident evolution
+    float* d_stream = nullptr;       // records and segment neighbours of the streamed evolution
     unsigned int* d_barrier = nullptr;  // its grid-barrier counter
     int max_tiles = 0;               // tiles the exchange buffer serves (the SM count)
     long long evolve_wait_limit = 0;  // test hook of the resident evolution's barrier waits
@@ -308,10 +309,30 @@ kaze_status enqueue_build(kaze_handle* h, const float* d_img, int w, int hh, int
         return KAZE_OK;
     }
     KZ_LAUNCH(h, KK_PRESMOOTH, kz::launch_gaussian(d_img, pitch_elems, level_ptr(h, 0), P, w, hh, h->taps0, st));
-    // with k measured here, |grad(G * L_0)|^2 stays in the conductance plane
-    // and the first conductance is computed from it
-    const bool m2 = h->opt.k_override <= 0.f;
+    // the streamed tile passes when asked for (the line kernels are faster
+    // for the images beyond one tile per SM)
+    const bool streamed = !resident && h->N > 1 && !h->surrogate && h->opt.scheme == KAZE_SCHEME_AOS &&
+                          h->opt.aos_solver == KAZE_AOS_STREAMED && kz::evolve_stream_fits(w, hh, h->tapsd.r);
+    // with k measured here and the line kernels, |grad(G * L_0)|^2 stays in
+    // the conductance plane and the first conductance is computed from it
+    const bool m2 = h->opt.k_override <= 0.f && !streamed;
     KZ_CHECK(enqueue_contrast(h, level_ptr(h, 0), P, w, hh, m2 ? h->g : nullptr));
+    if (streamed) {
+        for (int i = 1; i < h->N; ++i) {
+            KZ_LAUNCH(h, KK_STREAM_A, kz::launch_stream_pass(0, i, h->levels, h->cur_plane, P, w, hh, h->N, h->t,
+                                                             h->d_k, h->tapsd, h->opt.diffusivity, h->g,
+                                                             h->d_stream, st));
+            KZ_LAUNCH(h, KK_STREAM_X, kz::launch_stream_pass(1, i, h->levels, h->cur_plane, P, w, hh, h->N, h->t,
+                                                             h->d_k, h->tapsd, h->opt.diffusivity, h->g,
+                                                             h->d_stream, st));
+            KZ_LAUNCH(h, KK_STREAM_B, kz::launch_stream_pass(2, i, h->levels, h->cur_plane, P, w, hh, h->N, h->t,
+                                                             h->d_k, h->tapsd, h->opt.diffusivity, h->g,
+                                                             h->d_stream, st));
+        }
+        h->built = true;
+        h->responded = false;
+        return KAZE_OK;
+    }
     auto conductance = [&](int i, const float* Lp, float* zero) -> kaze_status {
         if (i == 1 && m2)
             KZ_LAUNCH(h, KK_CONDUCTANCE, kz::launch_cond_m2(h->g, zero, P, w, hh, h->d_k, h->opt.diffusivity, st));
@@ -614,7 +635,7 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
         return create_fail(KAZE_ERR_INVALID_ARG, "fed_tau_max must lie in (0, 0.25]");
     if (o.extrema_window != KAZE_EXTREMA_3X3 && o.extrema_window != KAZE_EXTREMA_SIGMA_WINDOW)
         return create_fail(KAZE_ERR_INVALID_ARG, "unknown extrema window");
-    if (o.aos_solver != KAZE_AOS_AUTO && o.aos_solver != KAZE_AOS_LINES)
+    if (o.aos_solver != KAZE_AOS_AUTO && o.aos_solver != KAZE_AOS_LINES && o.aos_solver != KAZE_AOS_STREAMED)
         return create_fail(KAZE_ERR_INVALID_ARG, "unknown AOS solver");
     if (max_w < 3 || max_h < 3 || max_w > 16384 || max_h > 16384)
         return create_fail(KAZE_ERR_INVALID_ARG, "max_w and max_h must be in 3..16384");
@@ -711,6 +732,7 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t off_xchg = bytes;   bytes += al(sizeof(float) * kz::evolve_exchange_floats(sms));
+    const size_t off_strm = bytes;   bytes += al(sizeof(float) * kz::evolve_stream_floats(max_w, max_h));
     cudaError_t e = cudaMalloc(&h->arena, bytes);
     if (e != cudaSuccess) {
         delete h;
@@ -739,6 +761,7 @@ KAZE_API kaze_status kaze_create(const kaze_options* opt, int max_w, int max_h, 
     h->d_dkp = (kaze_keypoint*)(a + off_dkp);
     h->d_desc = (float*)(a + off_desc);
     h->d_exchange = sms > 0 ? (float*)(a + off_xchg) : nullptr;
+    h->d_stream = (float*)(a + off_strm);
     h->max_tiles = sms;
     e = cudaMallocHost(&h->h_count, 2 * sizeof(unsigned int));
     if (e != cudaSuccess) {

@@ -239,6 +239,17 @@ struct EvolveImage {
     float* exchange = nullptr;
     unsigned int* barrier = nullptr;
 };
+// The streamed form for images whose tiles exceed one per SM (up to 64 x 64
+// tiles): each step as three launches, pass 0 (conductance and records of
+// every tile; g to the plane `g`), pass 1 (every segment's outside
+// neighbours from its line's records), pass 2 (the re-solves, L_lev to its
+// plane), for lev = 1 .. n_levels - 1 in order.  `scratch` holds
+// evolve_stream_floats(w, h) floats; *d_k holds the contrast factor.
+size_t evolve_stream_floats(int max_w, int max_h);
+bool evolve_stream_fits(int w, int h, int radius);
+cudaError_t launch_stream_pass(int pass, int lev, float* levels, long long plane, int pitch, int w, int h,
+                               int n_levels, const double* t, float* d_k, const GaussTaps& taps, int diffusivity,
+                               float* g, float* scratch, cudaStream_t st);
 size_t evolve_params_bytes();
 bool evolve_batch_params(void* out, const EvolveImage& im, int n_levels, const double* t, const GaussTaps& taps,
                          int diffusivity, int* status, long long wait_limit, int stall_tile);

@@ -32,6 +32,7 @@ EXTREMA_3X3 = 0
 EXTREMA_SIGMA_WINDOW = 1
 AOS_AUTO = 0
 AOS_LINES = 1
+AOS_STREAMED = 2
 
 
 class KazeError(RuntimeError):

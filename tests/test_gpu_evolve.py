@@ -97,10 +97,46 @@ def test_resident_and_line_kernels_at_1920x1200(kz):
 
 
 def test_resident_too_large_falls_back_to_lines(kz):
-    # 32 x 26 tiles do not fit one per SM: the line kernels run
+    # 32 x 26 tiles do not fit one per SM: the line kernels run; the streamed
+    # tile passes (three launches a step) when asked for
+    x = torch.rand(3072, 4096, device="cuda")
     with kz.Kaze(4096, 3072, octaves=1, sublevels=2) as kh:
-        prof = kh.profile(torch.rand(3072, 4096, device="cuda"))
-    assert prof["front_evolve"][1] == 0 and prof["aos_rows"][1] == 1
+        prof = kh.profile(x)
+    assert prof["front_evolve"][1] == 0 and prof["stream_a"][1] == 0 and prof["aos_rows"][1] == 1
+    with kz.Kaze(4096, 3072, octaves=1, sublevels=2, aos_solver=kz.AOS_STREAMED) as kh:
+        prof = kh.profile(x)
+    assert prof["aos_rows"][1] == 0
+    assert prof["stream_a"][1] == 1 and prof["stream_x"][1] == 1 and prof["stream_b"][1] == 1
+
+
+@pytest.mark.parametrize("shape", [(120, 128), (121, 129), (131, 257), (240, 384), (3, 3), (7, 300),
+                                   (300, 7), (16, 17)])
+def test_streamed_scale_space_against_oracle(kz, shape):
+    """The streamed tile passes (forced) against the oracle: one tile, ragged
+    tiles, lines shorter than a chunk."""
+    h, w = shape
+    img = synth.image(w, h, 40 + h + w) if min(h, w) >= 16 else \
+        np.random.default_rng(h * 1000 + w).random(shape).astype(np.float32)
+    k = k_of(img)
+    lv_g, prof = gpu_levels(kz, img, 2, 4, k, aos_solver=kz.AOS_STREAMED)
+    assert prof["stream_b"][1] == 7 and prof["front_evolve"][1] == 0, prof
+    lv_r = oracle_levels(img, 2, 4, k)
+    err = np.max(np.abs(lv_g - lv_r), axis=(1, 2))
+    assert np.all(err <= SCALE_TOL), err
+
+
+def test_streamed_g1_and_1920x1200_against_oracle(kz):
+    img = synth.image(250, 190, 77)
+    k = k_of(img)
+    lv_g, _ = gpu_levels(kz, img, 2, 4, k, diffusivity=kz.G1, aos_solver=kz.AOS_STREAMED)
+    lv_r = oracle_levels(img, 2, 4, k, diffusivity=oracle.G1)
+    assert np.max(np.abs(lv_g - lv_r)) <= SCALE_TOL
+    img = synth.workload_image("1920x1200")
+    k = k_of(img)
+    lv_g, _ = gpu_levels(kz, img, 4, 4, k, aos_solver=kz.AOS_STREAMED)
+    lv_r = oracle_levels(img, 4, 4, k)
+    err = np.max(np.abs(lv_g - lv_r), axis=(1, 2))
+    assert np.all(err <= SCALE_TOL), err
 
 
 def test_stalled_barrier_times_out_and_the_handle_recovers(kz):

@@ -2,8 +2,8 @@
 (needs a GB300; the oracle runs its independent loops on every host core):
 
 * the 4096x3072 image with its sinusoidal texture, 4 x 4 levels: every
-  level, every response and the keypoints (the line kernels: its 32 x 26
-  tiles exceed one a SM);
+  level, every response and the keypoints, through the line kernels (its
+  32 x 26 tiles exceed one an SM) and through the streamed tile passes;
 * two members of the 64-image mixed-size batch (a 640x480 and a 1280x720
   image) through the work-queue launch and through the resident evolution
   of the whole batch, against the oracle's detection of each;
@@ -64,15 +64,17 @@ def check_levels_responses(lv_g, D_g, lv_r, D_r):
         assert derr <= DOH_REL_TOL * dmax + 1e-12, (i, derr / dmax)
 
 
-def test_pipeline_4096x3072_against_oracle(kz):
+@pytest.mark.parametrize("solver", ["auto", "streamed"])
+def test_pipeline_4096x3072_against_oracle(kz, solver):
     img = synth.workload_image("4096x3072")
     h, w = img.shape
     k_ref, hmax = oracle_k(img)
-    with kz.Kaze(w, h, octaves=4, sublevels=4) as k:
+    sv = kz.AOS_STREAMED if solver == "streamed" else kz.AOS_AUTO
+    with kz.Kaze(w, h, octaves=4, sublevels=4, aos_solver=sv) as k:
         k.build_scale_space(dev(img))
         assert abs(k.contrast() - k_ref) <= hmax / 300 * 1.0001 + 1e-7
     kf = float(np.float32(k_ref))
-    with kz.Kaze(w, h, octaves=4, sublevels=4, k_override=kf) as k:
+    with kz.Kaze(w, h, octaves=4, sublevels=4, k_override=kf, aos_solver=sv) as k:
         kp_g = k.detect(dev(img))
         lv_g = k.levels().cpu().numpy().astype(np.float64)
         D_g = k.responses().cpu().numpy().astype(np.float64)
