@@ -394,6 +394,10 @@ __global__ void __launch_bounds__(128) k_aos_rows(const float* __restrict__ L, c
     const bool ok = !active || mbar_wait_bounded(&bars[r], 0);
     if (!__syncthreads_and(ok)) {  // same decision in every thread
         if (threadIdx.x == 0) atomicOr(status, 1);
+        // the row's copies still in flight land (bounded wait) before the CTA
+        // gives up its shared memory
+        if (active && part == 0 && lane == 0) mbar_wait_bounded(&bars[r], 0);
+        __syncthreads();
         return;
     }
 
@@ -469,7 +473,9 @@ __global__ void __launch_bounds__(COLS * 32 * NW)
     float* eq0 = td + (size_t)RS * COLS;
     float* eqc = eq0 + (size_t)c * 8 * P;  // this column's equations
 
+    __shared__ int s_fail;
     if (tid == 0) {
+        s_fail = 0;
 #pragma unroll
         for (int b = 0; b < NB; ++b) mbar_init(&bars[b], 1);
 #pragma unroll
@@ -489,8 +495,11 @@ __global__ void __launch_bounds__(COLS * 32 * NW)
         const int b_hi = min(j0 + M, RS - 1) / 256;
         for (int b = b_lo; b <= b_hi && ok; ++b) ok = mbar_wait_bounded(&bars[b], 0);
     }
-    if (!__all_sync(FULL, ok)) {  // a wait ran out: every warp still meets the barriers below
-        if ((tid & 31) == 0) atomicOr(status, 1);
+    if (!__all_sync(FULL, ok)) {  // a wait ran out: every warp still meets the barrier below
+        if ((tid & 31) == 0) {
+            atomicOr(status, 1);
+            s_fail = 1;
+        }
     }
     float* ce = tg + (size_t)j0 * COLS + c;
     float* cd = td + (size_t)j0 * COLS + c;
@@ -510,6 +519,14 @@ __global__ void __launch_bounds__(COLS * 32 * NW)
     eqc[5 * P + p] = q.dF;
 
     __syncthreads();
+    if (s_fail) {
+        // a staging wait ran out (the status is set): the boxes still in
+        // flight land (bounded wait) before the CTA gives up its shared memory
+        if (tid == 0)
+            for (int b = 0; b < NB; ++b) mbar_wait_bounded(&bars[b], 0);
+        __syncthreads();
+        return;
+    }
     const int warp = tid >> 5, lane = tid & 31;
     if (warp < COLS) {  // warp `warp` solves column `warp`
         float* eqw = eq0 + (size_t)warp * 8 * P;
