@@ -275,6 +275,10 @@ __global__ void __launch_bounds__(FW * 32) k_fed_fused(const __grid_constant__ C
             }
         }
     }
+    // a staging wait ran out (the status is set): the warp's boxes still in
+    // flight land (bounded wait) before it leaves its shared memory
+    if (__any_sync(0xffffffffu, !ok) && lane == 0)
+        for (int b = 0; b < NB; ++b) aos::mbar_wait_bounded(&bars[warp][b], 0);
 }
 
 }  // namespace
