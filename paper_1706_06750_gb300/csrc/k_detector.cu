@@ -266,13 +266,10 @@ cudaError_t launch_extrema(const float* D, int pitch, long long plane_stride, in
     if (n < 3) return cudaSuccess;
     if (cand) {
         if (!cand->count || (cand->cap > 0 && !cand->list)) return cudaErrorInvalidValue;
-        static int sms = 0;
-        if (sms == 0) {
-            int dev = 0;
-            cudaError_t e = cudaGetDevice(&dev);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return e;
-        }
+        int dev = 0, sms = 0;  // the grid only sizes the grid-stride loop
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
         k_extrema_cand<<<4 * sms, 256, 0, st>>>(D, pitch, plane_stride, w, h, n, tab, dthreshold, edge_r, d_kp, cap,
                                                 d_count, *cand);
         return cudaGetLastError();

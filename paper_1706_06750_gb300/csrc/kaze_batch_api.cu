@@ -312,7 +312,7 @@ kaze_status prepare_resident(kaze_batch* b)
     KB_TRY(b, cudaMemcpy(b->d_off, off.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice));
     b->egrid = grid;
     b->waves = (int)wave_imgs.size();
-    if (!b->d_resident) {
+    if (!b->d_resident || !b->h_eparams) {
         auto al = [](size_t x) { return (x + 255) / 256 * 256; };
         size_t bytes = 0, max_plane = 0;
         std::vector<size_t> xoff(b->n);
@@ -323,16 +323,31 @@ kaze_status prepare_resident(kaze_batch* b)
         }
         const size_t off_bar = bytes;
         bytes += al(sizeof(unsigned) * b->n);
-        b->cand_cap = (unsigned)std::min<size_t>(std::max<size_t>((size_t)b->N * max_plane / 16, 65536), 1u << 30);
+        const unsigned cand_cap =
+            (unsigned)std::min<size_t>(std::max<size_t>((size_t)b->N * max_plane / 16, 65536), 1u << 30);
         const size_t off_cand = bytes;
-        bytes += al(sizeof(unsigned long long) * b->cand_cap) * kaze_batch::kResBranches;
+        bytes += al(sizeof(unsigned long long) * cand_cap) * kaze_batch::kResBranches;
         const size_t off_ccnt = bytes;
         bytes += al(sizeof(unsigned) * kaze_batch::kResBranches);
-        b->eparams_bytes = (kz::evolve_params_bytes() + 15) / 16 * 16;
+        const size_t pbytes = (kz::evolve_params_bytes() + 15) / 16 * 16;
         const size_t off_par = bytes;
-        bytes += al(b->eparams_bytes * b->n);
-        KB_TRY(b, cudaMalloc(&b->d_resident, bytes));
-        KB_TRY(b, cudaMallocHost(&b->h_eparams, b->eparams_bytes * b->n));
+        bytes += al(pbytes * b->n);
+        // allocated together, kept only when both succeed
+        void* dres = nullptr;
+        void* hpar = nullptr;
+        cudaError_t e = cudaMalloc(&dres, bytes);
+        if (e == cudaSuccess) e = cudaMallocHost(&hpar, pbytes * b->n);
+        if (e != cudaSuccess) {
+            if (dres) cudaFree(dres);
+            return bfail(b, e == cudaErrorMemoryAllocation ? KAZE_ERR_OOM : KAZE_ERR_CUDA,
+                         std::string("resident batch buffers: ") + cudaGetErrorName(e));
+        }
+        if (b->d_resident) cudaFree(b->d_resident);
+        if (b->h_eparams) cudaFreeHost(b->h_eparams);
+        b->d_resident = dres;
+        b->h_eparams = hpar;
+        b->eparams_bytes = pbytes;
+        b->cand_cap = cand_cap;
         char* a = (char*)b->d_resident;
         b->exchange.resize(b->n);
         for (int i = 0; i < b->n; ++i) b->exchange[i] = (float*)(a + xoff[i]);
@@ -340,11 +355,11 @@ kaze_status prepare_resident(kaze_batch* b)
         b->d_cand = (unsigned long long*)(a + off_cand);
         b->d_cand_count = (unsigned*)(a + off_ccnt);
         b->d_eparams = a + off_par;
-        for (int k = 0; k < kaze_batch::kResBranches; ++k)
-            KB_TRY(b, cudaStreamCreateWithFlags(&b->res_s[k], cudaStreamNonBlocking));
-        for (int k = 0; k <= kaze_batch::kResBranches; ++k)
-            KB_TRY(b, cudaEventCreateWithFlags(&b->res_ev[k], cudaEventDisableTiming));
     }
+    for (int k = 0; k < kaze_batch::kResBranches; ++k)
+        if (!b->res_s[k]) KB_TRY(b, cudaStreamCreateWithFlags(&b->res_s[k], cudaStreamNonBlocking));
+    for (int k = 0; k <= kaze_batch::kResBranches; ++k)
+        if (!b->res_ev[k]) KB_TRY(b, cudaEventCreateWithFlags(&b->res_ev[k], cudaEventDisableTiming));
     return refresh_resident(b);
 }
 
